@@ -1,0 +1,287 @@
+"""Oracle for the Marsaglia generators of arXiv:1101.1846 (Hissoiny, Despres
+and Ozell, "Using graphics processing units to generate random numbers").
+
+TEST INFRASTRUCTURE ONLY.  A thin ctypes wrapper around ``oracle.c``: plain,
+slow, single-threaded C that states each recurrence literally.  Only
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and
+reference legs may import this package; the product library never does and
+shares no code with it.
+
+Kinds: 0 = MWC base 2^32 (Eq. 2-3), 1 = xor128 (Marsaglia 2003), 2 = KISS
+(MWC + xorshift32 of Eq. 6 + LCG of Eq. 7, summed mod 2^32).
+Formats: 0 = uint32, 1 = float32 uniform (u >> 8) * 2^-24.
+State: four uint32 words per stream (see ``oracle.h``).
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes
+import multiprocessing as mp
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+BUILD = HERE / "_build"
+LIB = BUILD / "liboracle.so"
+SOURCES = [HERE / "oracle.c", HERE / "oracle.h"]
+
+MWC, XOR128, KISS = 0, 1, 2
+U32, F32 = 0, 1
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.c into a shared object (gcc, -O2, no vector flags)."""
+    BUILD.mkdir(exist_ok=True)
+    stale = not LIB.exists() or any(
+        s.stat().st_mtime > LIB.stat().st_mtime for s in SOURCES)
+    if force or stale:
+        tmp = BUILD / f"liboracle.{os.getpid()}.so"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                        "-Wall", "-Wextra", "-o", str(tmp),
+                        str(HERE / "oracle.c")], check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load(build())
+    return _lib
+
+
+@contextlib.contextmanager
+def using(path):
+    """Route every call through another build of oracle.c for the duration
+    of the block (the tests that plant a mistake in a copy use this)."""
+    global _lib
+    saved = _lib
+    _lib = _load(Path(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def compile_variant(src_text: str, out_path) -> Path:
+    """Compile a modified copy of oracle.c (tests only)."""
+    out_path = Path(out_path)
+    c = out_path.with_suffix(".c")
+    c.write_text(src_text)
+    (out_path.parent / "oracle.h").write_text((HERE / "oracle.h").read_text())
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o",
+                    str(out_path), str(c)], check=True)
+    return out_path
+
+
+def _load(path: Path):
+    L = ctypes.CDLL(str(path))
+    u32, u64, i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "oracle_mulmod_u64": (u64, [u64, u64, u64]),
+        "oracle_powmod_u64": (u64, [u64, u64, u64]),
+        "oracle_is_prime_u64": (i32, [u64]),
+        "oracle_is_safe_multiplier": (i32, [u64, i32]),
+        "oracle_multipliers": (u64, [i32, u64, u64, _u32p]),
+        "oracle_multipliers_range": (u64, [i32, u64, u64, _u32p, u64]),
+        "oracle_splitmix64": (u64, [_u64p]),
+        "oracle_seed_stream": (None, [i32, u32, u64, u64, _u32p]),
+        "oracle_seed_streams": (None, [i32, _u32p, u64, _u64p, u64, _u32p]),
+        "oracle_mwc_step": (u32, [u32, _u32p, _u32p, i32]),
+        "oracle_xor128_step": (u32, [_u32p]),
+        "oracle_xorshift32_step": (u32, [_u32p]),
+        "oracle_lcg_step": (u32, [_u32p]),
+        "oracle_kiss_step": (u32, [u32, _u32p]),
+        "oracle_step": (u32, [i32, u32, _u32p]),
+        "oracle_to_unit_f32": (ctypes.c_float, [u32]),
+        "oracle_stream": (None, [i32, u32, _u32p, u64, i32, ctypes.c_void_p]),
+        "oracle_generate": (None, [i32, u64, _u32p, _u32p, u64, i32,
+                                   ctypes.c_void_p]),
+        "oracle_mwc_period": (u64, [u32, u32, u32, i32, u64]),
+        "oracle_xorshift32_period": (u64, [u32]),
+        "oracle_lcg_period": (u64, [u32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def _p32(a: np.ndarray):
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_u32p)
+
+
+def _p64(a: np.ndarray):
+    assert a.dtype == np.uint64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_u64p)
+
+
+# ---------------------------------------------------------------- numbers
+def is_prime(n: int) -> bool:
+    return bool(lib().oracle_is_prime_u64(n))
+
+
+def is_safe_multiplier(a: int, log2b: int = 32) -> bool:
+    return bool(lib().oracle_is_safe_multiplier(a, log2b))
+
+
+def powmod(b: int, e: int, m: int) -> int:
+    return int(lib().oracle_powmod_u64(b, e, m))
+
+
+def multipliers_range(a_hi: int, a_lo: int, log2b: int = 32) -> np.ndarray:
+    """Every valid multiplier in [a_lo, a_hi], descending."""
+    cap = max(16, (a_hi - a_lo + 1) // 64 + 64)
+    while True:
+        out = np.zeros(cap, np.uint32)
+        n = int(lib().oracle_multipliers_range(log2b, a_hi, a_lo, _p32(out), cap))
+        if n <= cap:
+            return out[:n].copy()
+        cap = n
+
+
+def _range_worker(args):
+    a_hi, a_lo, log2b = args
+    return multipliers_range(a_hi, a_lo, log2b)
+
+
+def multipliers(k: int, log2b: int = 32, procs: int | None = None,
+                chunk: int = 1 << 22) -> np.ndarray:
+    """The first k valid multipliers below b, largest first (Sec. on MWC:
+    a*b - 1 a safe prime).  Large tables are searched over disjoint ranges
+    of a in worker processes (spawned, never forked) and concatenated in
+    order; each range is the same single-threaded scan."""
+    a_top = (1 << log2b) - 1
+    if k <= 16384 or (procs or 0) == 1:
+        out = np.zeros(k, np.uint32)
+        n = int(lib().oracle_multipliers(log2b, a_top, k, _p32(out)))
+        return out[:n]
+    procs = procs or os.cpu_count() or 1
+    ranges = []
+    hi = a_top
+    while hi >= 1:
+        lo = max(1, hi - chunk + 1)
+        ranges.append((hi, lo, log2b))
+        hi = lo - 1
+    parts, total = [], 0
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        for part in pool.imap(_range_worker, ranges):
+            parts.append(part)
+            total += len(part)
+            if total >= k:
+                pool.terminate()
+                break
+    return np.concatenate(parts)[:k]
+
+
+# ---------------------------------------------------------------- seeding
+def splitmix64(z: int) -> tuple[int, int]:
+    """One splitmix64 draw: returns (new_state, output)."""
+    s = ctypes.c_uint64(z)
+    r = lib().oracle_splitmix64(ctypes.byref(s))
+    return int(s.value), int(r)
+
+
+def seed_streams(kind: int, a: np.ndarray | None, seed: int,
+                 s_ids: np.ndarray) -> np.ndarray:
+    """Initial state (n, 4) uint32 of the streams with indices s_ids; a[i]
+    is the multiplier of stream s_ids[i]."""
+    s_ids = np.ascontiguousarray(s_ids, dtype=np.uint64)
+    n = len(s_ids)
+    st = np.zeros((n, 4), np.uint32)
+    ap = None
+    if kind != XOR128:
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        assert len(a) == n
+        ap = _p32(a)
+    lib().oracle_seed_streams(kind, ap, seed & (2**64 - 1), _p64(s_ids), n, _p32(st))
+    return st
+
+
+# ---------------------------------------------------------------- steps
+def mwc_step(a: int, x: int, c: int, log2b: int = 32) -> tuple[int, int]:
+    X, C = ctypes.c_uint32(x), ctypes.c_uint32(c)
+    lib().oracle_mwc_step(a, ctypes.byref(X), ctypes.byref(C), log2b)
+    return int(X.value), int(C.value)
+
+
+def _st(st):
+    arr = (ctypes.c_uint32 * 4)(*[int(v) for v in st])
+    return arr
+
+
+def xor128_step(st) -> tuple[int, list]:
+    arr = _st(st)
+    out = lib().oracle_xor128_step(arr)
+    return int(out), list(arr)
+
+
+def xorshift32_step(y: int) -> int:
+    Y = ctypes.c_uint32(y)
+    return int(lib().oracle_xorshift32_step(ctypes.byref(Y)))
+
+
+def lcg_step(z: int) -> int:
+    Z = ctypes.c_uint32(z)
+    return int(lib().oracle_lcg_step(ctypes.byref(Z)))
+
+
+def kiss_step(a: int, st) -> tuple[int, list]:
+    arr = _st(st)
+    out = lib().oracle_kiss_step(a, arr)
+    return int(out), list(arr)
+
+
+def to_unit_f32(u: int) -> float:
+    return float(np.float32(lib().oracle_to_unit_f32(u)))
+
+
+# ---------------------------------------------------------------- calls
+def generate(kind: int, a: np.ndarray | None, state: np.ndarray,
+             n_per_stream: int, fmt: int) -> tuple[np.ndarray, np.ndarray]:
+    """One generate call over len(state) streams.  Returns (out, new_state)
+    with out of shape (n_per_stream, n_streams): out[j, s] is output j of
+    stream s (the stream-interleaved layout)."""
+    state = np.array(state, dtype=np.uint32, order="C", copy=True)
+    n = state.shape[0]
+    out = np.zeros((n_per_stream, n), np.uint32 if fmt == U32 else np.float32)
+    ap = None
+    if kind != XOR128:
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        assert len(a) >= n
+        ap = _p32(a)
+    lib().oracle_generate(kind, n, ap, _p32(state), n_per_stream, fmt,
+                          out.ctypes.data_as(ctypes.c_void_p))
+    return out, state
+
+
+def stream(kind: int, a: int, st, n: int, fmt: int) -> tuple[np.ndarray, np.ndarray]:
+    """n outputs of one stream, contiguous; returns (out, new_state)."""
+    arr = np.array(st, dtype=np.uint32)
+    out = np.zeros(n, np.uint32 if fmt == U32 else np.float32)
+    lib().oracle_stream(kind, a, _p32(arr), n, fmt,
+                        out.ctypes.data_as(ctypes.c_void_p))
+    return out, arr
+
+
+# ---------------------------------------------------------------- periods
+def mwc_period(a: int, x0: int, c0: int, log2b: int, limit: int) -> int:
+    return int(lib().oracle_mwc_period(a, x0, c0, log2b, limit))
+
+
+def xorshift32_period(y0: int) -> int:
+    return int(lib().oracle_xorshift32_period(y0))
+
+
+def lcg_period(z0: int) -> int:
+    return int(lib().oracle_lcg_period(z0))

@@ -1,0 +1,408 @@
+/*
+ * Oracle for Hissoiny, Despres & Ozell, "Using graphics processing units to
+ * generate random numbers" (arXiv:1101.1846).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, single-threaded C that writes the
+ * paper's recurrences out literally, one stream and one step at a time, with
+ * no blocking, unrolling or reordering.  Only tests/, __graft_entry__.smoke()
+ * and bench.py's CPU baseline / reference arm may load it.  It shares no code
+ * with the CUDA library.
+ *
+ * Parity status of each part (what pins it is in tests/test_oracle_pins.py):
+ *   primality, multiplier search ... pinned (392 count of Sec. "Methods /
+ *                                    multiply-with-carry"; brute force)
+ *   MWC step ....................... pinned (Lehmer closed form; periods)
+ *   xor128 step .................... pinned (full period 2^128-1 over GF(2))
+ *   xorshift32 step ................ pinned (period 2^32-1); its shift ORDER
+ *                                    is parity unpinned (both orders of Eq. 6
+ *                                    have full period)
+ *   LCG step ....................... pinned (Eq. 7 constants; period 2^32)
+ *   KISS combination ............... pinned (sum of independently stepped parts)
+ *   FP32 uniform ................... pinned (exactness, range)
+ *   splitmix64 seeding ............. increment pinned (golden ratio); the
+ *                                    finaliser constants are parity unpinned
+ *                                    beyond a published test value
+ */
+#include "oracle.h"
+
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Number theory for the multiplier condition (Sec. "multiply-with-carry"
+ * of the background: a*b-1 must be a safe prime).                        */
+/* ------------------------------------------------------------------ */
+
+uint64_t oracle_mulmod_u64(uint64_t a, uint64_t b, uint64_t m)
+{
+    return (uint64_t)(((unsigned __int128)a * b) % m);
+}
+
+uint64_t oracle_powmod_u64(uint64_t base, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    base %= m;
+    while (e) {
+        if (e & 1)
+            r = oracle_mulmod_u64(r, base, m);
+        base = oracle_mulmod_u64(base, base, m);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* Odd primes below 1024, by a sieve of Eratosthenes on first use. */
+static int g_small_primes[200];
+static int g_n_small_primes = 0;
+
+static void init_small_primes(void)
+{
+    if (g_n_small_primes)
+        return;
+    char composite[1024] = {0};
+    int n = 0;
+    for (int i = 3; i < 1024; i += 2) {
+        if (composite[i])
+            continue;
+        g_small_primes[n++] = i;
+        for (int j = i * i; j < 1024; j += 2 * i)
+            composite[j] = 1;
+    }
+    g_n_small_primes = n;
+}
+
+/* Trial division by 2 and the odd primes below 1024: returns 0 when n is
+ * composite (or < 2), 1 when n is proven prime (n < 1024^2 with no factor
+ * found), 2 when undecided. */
+static int small_factor_verdict(uint64_t n)
+{
+    init_small_primes();
+    if (n < 2)
+        return 0;
+    if (n % 2 == 0)
+        return n == 2;
+    for (int i = 0; i < g_n_small_primes; ++i) {
+        uint64_t l = (uint64_t)g_small_primes[i];
+        if (n % l == 0)
+            return n == l;
+    }
+    return n < 1024ull * 1024ull ? 1 : 2;
+}
+
+/* Deterministic Miller-Rabin for every n < 2^64: the first twelve primes as
+ * bases are a proven deterministic set below 3.3e24 (Sorenson and Webster,
+ * "Strong pseudoprimes to twelve prime bases", Math. Comp. 2017).  n must be
+ * odd and larger than 37. */
+static const uint64_t k_mr_bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+
+static int miller_rabin(uint64_t n)
+{
+    /* n - 1 = d * 2^r with d odd */
+    uint64_t d = n - 1;
+    int r = 0;
+    while ((d & 1) == 0) {
+        d >>= 1;
+        ++r;
+    }
+    for (int i = 0; i < 12; ++i) {
+        uint64_t x = oracle_powmod_u64(k_mr_bases[i], d, n);
+        if (x == 1 || x == n - 1)
+            continue;
+        int witness = 1;
+        for (int k = 1; k < r; ++k) {
+            x = oracle_mulmod_u64(x, x, n);
+            if (x == n - 1) {
+                witness = 0;
+                break;
+            }
+        }
+        if (witness)
+            return 0;
+    }
+    return 1;
+}
+
+int oracle_is_prime_u64(uint64_t n)
+{
+    int v = small_factor_verdict(n);
+    if (v != 2)
+        return v;
+    return miller_rabin(n);
+}
+
+/* The multiplier condition: p = a*b - 1 is a safe prime, i.e. p and
+ * (p - 1)/2 are both prime, with b = 2^log2b.  Both numbers are trial
+ * divided before either gets the slower Miller-Rabin test; the verdict is
+ * the same as oracle_is_prime_u64(q) && oracle_is_prime_u64(p). */
+int oracle_is_safe_multiplier(uint64_t a, int log2b)
+{
+    if (a == 0)
+        return 0;
+    uint64_t p = a * ((uint64_t)1 << log2b) - 1;
+    uint64_t q = (p - 1) / 2;
+    int vq = small_factor_verdict(q);
+    if (vq == 0)
+        return 0;
+    int vp = small_factor_verdict(p);
+    if (vp == 0)
+        return 0;
+    return (vq == 1 || miller_rabin(q)) && (vp == 1 || miller_rabin(p));
+}
+
+/* The first k valid multipliers scanning a = a_top, a_top - 1, ..., 1.
+ * Returns how many were found (k unless the scan reached a = 0). */
+uint64_t oracle_multipliers(int log2b, uint64_t a_top, uint64_t k, uint32_t *out)
+{
+    uint64_t found = 0;
+    for (uint64_t a = a_top; a >= 1 && found < k; --a) {
+        if (oracle_is_safe_multiplier(a, log2b))
+            out[found++] = (uint32_t)a;
+    }
+    return found;
+}
+
+/* Every valid multiplier in [a_lo, a_hi], in descending order.  Returns the
+ * count; only the first `cap` are written.  Consecutive ranges concatenate
+ * to the same list oracle_multipliers produces. */
+uint64_t oracle_multipliers_range(int log2b, uint64_t a_hi, uint64_t a_lo,
+                                  uint32_t *out, uint64_t cap)
+{
+    uint64_t found = 0;
+    if (a_lo < 1)
+        a_lo = 1;
+    for (uint64_t a = a_hi; a >= a_lo; --a) {
+        if (oracle_is_safe_multiplier(a, log2b)) {
+            if (found < cap)
+                out[found] = (uint32_t)a;
+            ++found;
+        }
+        if (a == a_lo)
+            break;
+    }
+    return found;
+}
+
+/* ------------------------------------------------------------------ */
+/* Seeding.  The paper gives every thread its own seeds (parametrisation,
+ * Sec. "Parallelizing RNGs" and the MWC/KISS kernel descriptions) without
+ * saying how they are made; they are drawn here from splitmix64 (Steele,
+ * Lea and Flood, "Fast splittable pseudorandom number generators", 2014)
+ * started at seed + stream index.                                       */
+/* ------------------------------------------------------------------ */
+
+uint64_t oracle_splitmix64(uint64_t *z)
+{
+    *z += 0x9E3779B97F4A7C15ull;
+    uint64_t r = *z;
+    r = (r ^ (r >> 30)) * 0xBF58476D1CE4E5B9ull;
+    r = (r ^ (r >> 27)) * 0x94D049BB133111EBull;
+    return r ^ (r >> 31);
+}
+
+static uint32_t lo32(uint64_t v) { return (uint32_t)(v & 0xFFFFFFFFull); }
+static uint32_t hi32(uint64_t v) { return (uint32_t)(v >> 32); }
+
+/* MWC (x, c) from successive draws: c is reduced below a so that the state
+ * is one of the Lehmer-form states, and the two fixed points (0, 0) and
+ * (b - 1, a - 1) are skipped by drawing again. */
+static void seed_mwc(uint32_t a, uint64_t *z, uint32_t *x, uint32_t *c)
+{
+    for (;;) {
+        uint64_t r = oracle_splitmix64(z);
+        *x = lo32(r);
+        *c = hi32(r) % a;
+        int zero = (*x == 0 && *c == 0);
+        int top = (*x == 0xFFFFFFFFu && *c == a - 1);
+        if (!zero && !top)
+            return;
+    }
+}
+
+void oracle_seed_stream(int kind, uint32_t a, uint64_t seed, uint64_t s,
+                        uint32_t st[4])
+{
+    uint64_t z = seed + s;
+    memset(st, 0, 4 * sizeof(uint32_t));
+    if (kind == 0) {
+        seed_mwc(a, &z, &st[0], &st[1]);
+    } else if (kind == 1) {
+        for (;;) {
+            uint64_t r0 = oracle_splitmix64(&z);
+            uint64_t r1 = oracle_splitmix64(&z);
+            st[0] = lo32(r0);
+            st[1] = hi32(r0);
+            st[2] = lo32(r1);
+            st[3] = hi32(r1);
+            if (st[0] | st[1] | st[2] | st[3])
+                return;
+        }
+    } else {
+        seed_mwc(a, &z, &st[0], &st[1]);
+        uint64_t r = oracle_splitmix64(&z);
+        st[2] = lo32(r);
+        st[3] = hi32(r);
+        while (st[2] == 0)
+            st[2] = lo32(oracle_splitmix64(&z));
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* The generators.                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Eq. 2-3: x_{n+1} = (a x_n + c_n) mod b, c_{n+1} = floor((a x_n + c_n)/b),
+ * written with the division and remainder themselves; b = 2^log2b. */
+uint32_t oracle_mwc_step(uint32_t a, uint32_t *x, uint32_t *c, int log2b)
+{
+    uint64_t b = (uint64_t)1 << log2b;
+    uint64_t t = (uint64_t)a * (uint64_t)(*x) + (uint64_t)(*c);
+    *x = (uint32_t)(t % b);
+    *c = (uint32_t)(t / b);
+    return *x;
+}
+
+/* xor128 (Marsaglia, "Xorshift RNGs", J. Stat. Softw. 8(14), 2003): state
+ * (x, y, z, w); t = x ^ (x << 11); the words shift down by one; the new w is
+ * w ^ (w >> 19) ^ t ^ (t >> 8), which is also the output. */
+uint32_t oracle_xor128_step(uint32_t st[4])
+{
+    uint32_t x = st[0];
+    uint32_t t = x ^ (x << 11);
+    st[0] = st[1];
+    st[1] = st[2];
+    st[2] = st[3];
+    uint32_t w = st[3];
+    st[3] = w ^ (w >> 19) ^ t ^ (t >> 8);
+    return st[3];
+}
+
+/* Eq. 6: the type-I xorshift with A1 = (I + L^13)(I + R^17)(I + L^5),
+ * applied as <<13, then >>17, then <<5. */
+uint32_t oracle_xorshift32_step(uint32_t *y)
+{
+    uint32_t v = *y;
+    v ^= v << 13;
+    v ^= v >> 17;
+    v ^= v << 5;
+    *y = v;
+    return v;
+}
+
+/* Eq. 7 with a = 69069, c = 1234567, m = 2^32. */
+uint32_t oracle_lcg_step(uint32_t *z)
+{
+    uint64_t m = (uint64_t)1 << 32;
+    *z = (uint32_t)((69069ull * (uint64_t)(*z) + 1234567ull) % m);
+    return *z;
+}
+
+/* KISS: each of the three parts advances once and the output is the sum of
+ * their new values mod 2^32. */
+uint32_t oracle_kiss_step(uint32_t a, uint32_t st[4])
+{
+    uint32_t m = oracle_mwc_step(a, &st[0], &st[1], 32);
+    uint32_t y = oracle_xorshift32_step(&st[2]);
+    uint32_t z = oracle_lcg_step(&st[3]);
+    return (uint32_t)(((uint64_t)m + y + z) % ((uint64_t)1 << 32));
+}
+
+uint32_t oracle_step(int kind, uint32_t a, uint32_t st[4])
+{
+    if (kind == 0)
+        return oracle_mwc_step(a, &st[0], &st[1], 32);
+    if (kind == 1)
+        return oracle_xor128_step(st);
+    return oracle_kiss_step(a, st);
+}
+
+/* Uniform in [0, 1): the top 24 bits of u as an integer times 2^-24.  Both
+ * the conversion (a 24-bit integer) and the power-of-two scaling are exact
+ * in binary32. */
+float oracle_to_unit_f32(uint32_t u)
+{
+    return (float)(u >> 8) * (1.0f / 16777216.0f);
+}
+
+/* One stream: n outputs written contiguously, state advanced in place. */
+void oracle_stream(int kind, uint32_t a, uint32_t st[4], uint64_t n, int fmt,
+                   void *out)
+{
+    for (uint64_t j = 0; j < n; ++j) {
+        uint32_t u = oracle_step(kind, a, st);
+        if (fmt == 0)
+            ((uint32_t *)out)[j] = u;
+        else
+            ((float *)out)[j] = oracle_to_unit_f32(u);
+    }
+}
+
+/* One generate call over all streams: output j of stream s goes to
+ * out[j * n_streams + s]; state holds 4 words per stream (st[4*s + w]). */
+void oracle_generate(int kind, uint64_t n_streams, const uint32_t *a,
+                     uint32_t *state, uint64_t n_per_stream, int fmt,
+                     void *out)
+{
+    for (uint64_t s = 0; s < n_streams; ++s) {
+        uint32_t *st = state + 4 * s;
+        uint32_t as = a ? a[s] : 0;
+        for (uint64_t j = 0; j < n_per_stream; ++j) {
+            uint32_t u = oracle_step(kind, as, st);
+            uint64_t idx = j * n_streams + s;
+            if (fmt == 0)
+                ((uint32_t *)out)[idx] = u;
+            else
+                ((float *)out)[idx] = oracle_to_unit_f32(u);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Brute-force periods.                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Steps until (x, c) returns to (x0, c0); 0 if not within `limit` steps. */
+uint64_t oracle_mwc_period(uint32_t a, uint32_t x0, uint32_t c0, int log2b,
+                           uint64_t limit)
+{
+    uint32_t x = x0, c = c0;
+    for (uint64_t n = 1; n <= limit; ++n) {
+        oracle_mwc_step(a, &x, &c, log2b);
+        if (x == x0 && c == c0)
+            return n;
+    }
+    return 0;
+}
+
+uint64_t oracle_xorshift32_period(uint32_t y0)
+{
+    uint32_t y = y0;
+    uint64_t n = 0;
+    do {
+        oracle_xorshift32_step(&y);
+        ++n;
+    } while (y != y0 && n <= 0x100000000ull);
+    return n;
+}
+
+uint64_t oracle_lcg_period(uint32_t z0)
+{
+    uint32_t z = z0;
+    uint64_t n = 0;
+    do {
+        oracle_lcg_step(&z);
+        ++n;
+    } while (z != z0 && n <= 0x100000001ull);
+    return n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Batch helpers for the Python wrapper (loops over the functions above). */
+/* ------------------------------------------------------------------ */
+
+/* Seeds the streams listed in s_ids (n of them); a[i] is the multiplier of
+ * stream s_ids[i] (ignored for xor128); st receives 4 words per stream. */
+void oracle_seed_streams(int kind, const uint32_t *a, uint64_t seed,
+                         const uint64_t *s_ids, uint64_t n, uint32_t *st)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        oracle_seed_stream(kind, a ? a[i] : 0, seed, s_ids[i], st + 4 * i);
+}

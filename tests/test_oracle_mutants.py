@@ -1,0 +1,68 @@
+"""Plants plausible mistakes in copies of oracle.c (on the CPU) and checks
+that the pins in test_oracle_pins.py catch each one."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = (oracle.HERE / "oracle.c").read_text()
+
+# (name, text in oracle.c, replacement, pin expected to fail)
+MUTANTS = [
+    ("xor128 shift 11->10", "uint32_t t = x ^ (x << 11);", "uint32_t t = x ^ (x << 10);",
+     pins.check_xor128_full_period_gf2),
+    ("xor128 shift 19->18", "st[3] = w ^ (w >> 19)", "st[3] = w ^ (w >> 18)",
+     pins.check_xor128_full_period_gf2),
+    ("xor128 drops t>>8", "(w >> 19) ^ t ^ (t >> 8);", "(w >> 19) ^ t;",
+     pins.check_xor128_full_period_gf2),
+    ("xor128 outputs old w", "    return st[3];\n}\n\n/* Eq. 6",
+     "    return w;\n}\n\n/* Eq. 6", pins.check_xor128_output_is_new_last_word),
+    ("xorshift32 shift 17->15", "v ^= v >> 17;", "v ^= v >> 15;",
+     pins.check_xorshift32_full_period_gf2),
+    ("xorshift32 right/left swapped", "v ^= v >> 17;", "v ^= v << 17;",
+     pins.check_xorshift32_full_period_gf2),
+    ("LCG increment off by one", "+ 1234567ull", "+ 1234568ull",
+     pins.check_lcg_constants),
+    ("LCG multiplier typo", "69069ull *", "69096ull *",
+     pins.check_lcg_constants),
+    ("MWC x and carry transposed",
+     "*x = (uint32_t)(t % b);\n    *c = (uint32_t)(t / b);",
+     "*c = (uint32_t)(t % b);\n    *x = (uint32_t)(t / b);",
+     pins.check_mwc_lehmer_closed_form),
+    ("MWC carry dropped", "(uint64_t)a * (uint64_t)(*x) + (uint64_t)(*c)",
+     "(uint64_t)a * (uint64_t)(*x)", pins.check_mwc_period_base_2_16),
+    ("KISS in the xor form", "((uint64_t)m + y + z)", "((uint64_t)(m ^ z) + y)",
+     pins.check_kiss_is_sum_of_parts),
+    ("KISS drops the LCG", "((uint64_t)m + y + z)", "((uint64_t)m + y)",
+     pins.check_kiss_is_sum_of_parts),
+    ("uniform uses 23 bits", "(float)(u >> 8)", "(float)(u >> 9)",
+     pins.check_uniform_exact),
+    ("Miller-Rabin with 7 bases", "for (int i = 0; i < 12; ++i) {\n        uint64_t x",
+     "for (int i = 0; i < 7; ++i) {\n        uint64_t x",
+     pins.check_strong_pseudoprime),
+    ("safe-prime test drops q", "return (vq == 1 || miller_rabin(q)) && ",
+     "return 1 && ", pins.check_mwc16_multiplier_count),
+    ("trial division misses 3", "for (int i = 3; i < 1024; i += 2)",
+     "for (int i = 5; i < 1024; i += 2)", pins.check_mwc16_multipliers_brute_force),
+]
+
+
+@pytest.mark.parametrize("name,old,new,check", MUTANTS,
+                         ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(tmp_path, name, old, new, check):
+    assert SRC.count(old) == 1, f"mutation anchor not unique: {name}"
+    so = oracle.compile_variant(SRC.replace(old, new), tmp_path / "mutant.so")
+    with oracle.using(so):
+        with pytest.raises(AssertionError):
+            check()
+
+
+def test_unmutated_copy_passes_every_check(tmp_path):
+    so = oracle.compile_variant(SRC, tmp_path / "same.so")
+    with oracle.using(so):
+        for _, _, _, check in MUTANTS:
+            check()
+    assert np.uint32(1)
