@@ -1,0 +1,379 @@
+"""Benchmark: GSamples/s written to HBM by the generate kernels, with the
+roofline of the dominant kernel, an end-to-end figure through the host-
+delivery call, the oracle on the host cores, and clocks seen meanwhile.
+
+Workload (full device): MWC, xor128 and KISS at 2^22 streams x 1024 outputs
+per stream per call, uint32 and FP32, state carried on the device from call
+to call.  One step = one call of each (kind, format) pair: 6 launches,
+6 x 2^32 samples, 96 GiB written.  Each call's 16 GiB output is far larger
+than L2, so no flush is needed between calls.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "GSamples/s (uint32/FP32 to HBM) and % of HBM-write/INT32 roofline; batched vs plain"
+UNIT = "GSamples/s"
+KINDS = (0, 1, 2)
+FMTS = (0, 1)
+KNAME = {0: "mwc", 1: "xor128", 2: "kiss"}
+FNAME = {0: "u32", 1: "f32"}
+STATE_WORDS = {0: 2, 1: 4, 2: 4}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-streams", type=int, default=1 << 22)
+    p.add_argument("--n-per-stream", type=int, default=1024)
+    p.add_argument("--seed", type=int, default=42)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    return p.parse_args()
+
+
+def alg_bytes(kind: int, n: int, steps: int) -> int:
+    """Bytes one launch must move: the outputs, the state read and written
+    back, and the multipliers read (MWC, KISS)."""
+    w = STATE_WORDS[kind]
+    return 4 * n * steps + 2 * 4 * w * n + (4 * n if kind != 1 else 0)
+
+
+def peaks():
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        d = json.loads(f.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("gen_body.cuh", "generate.cu", "gbrng.cuh"):
+        h.update((ROOT / "paper_1101_1846_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    f = ROOT / "profiles" / "dram_traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    rec = d.get("kernels", {}).get(kernel, {})
+    if rec.get("workload") != workload:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_selector(torch) -> str | None:
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        u = str(getattr(props, "uuid", "") or "")
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- oracle
+def _oracle_worker(args):
+    kind, fmt, m, steps, seed, a = args
+    import numpy as np
+
+    import oracle
+    st = oracle.seed_streams(kind, a if kind != 1 else None, seed, np.arange(m))
+    t0 = time.perf_counter()
+    oracle.generate(kind, a if kind != 1 else None, st, steps, fmt)
+    return m * steps, time.perf_counter() - t0
+
+
+def cpu_baseline(steps_per_stream: int, streams_per_job: int = 1 << 13, seed: int = 42):
+    """The oracle as it stands, one single-threaded process per host core,
+    each on its own slice (streams_per_job streams x steps_per_stream) of
+    every (kind, format) pair of the workload.  Returns GSamples/s over the
+    wall time of the parallel region."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    a = oracle.multipliers(streams_per_job, 32)
+    jobs = [(k, f, streams_per_job, steps_per_stream, seed + r * streams_per_job, a)
+            for r in range(cores) for k in KINDS for f in FMTS]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [(0, 0, 64, 4, 1, a[:64])] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    samples = sum(r[0] for r in res)
+    cpu_s = sum(r[1] for r in res)
+    return {"value": samples / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x 6 (kind, fmt) slices of {streams_per_job} streams "
+                      f"x {steps_per_stream} outputs ({samples / 1e6:.0f} M samples, "
+                      f"{cpu_s:.1f} CPU-s, {wall:.1f} s wall)",
+            "samples": samples, "wall_s": wall, "np_version": np.__version__}
+
+
+# ------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps_per_stream = min(args.n_per_stream, 256)
+    vals = []
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline(steps_per_stream, 1 << 11)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cb = cpu_baseline(steps_per_stream, 1 << 11)
+        vals.append(cb["samples"] / cb["wall_s"])
+    total = time.perf_counter() - t0
+    value = statistics.median(vals) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"full_2^22x{args.n_per_stream}",
+                   "note": "each step a bounded slice of the same workload on the host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"],
+                         "kind": "oracle", "sample": cb["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import ctypes
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1101_1846_gb300 import capi
+    from paper_1101_1846_gb300.generator import Generator
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    capi.lib()
+    n, steps = args.n_streams, args.n_per_stream
+    workload = f"full_2^{n.bit_length() - 1}x{steps}" if n & (n - 1) == 0 else f"{n}x{steps}"
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # weak scaling: every rank owns its own n streams, seeds shifted by rank*n
+    gens = {k: Generator(k, n, args.seed + rank * n) for k in KINDS}
+    out = torch.empty((steps, n), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    pairs = [(k, f) for k in KINDS for f in FMTS]
+
+    def one_step(events=None):
+        for k, f in pairs:
+            if events is not None:
+                events[(k, f)][0].append(torch.cuda.Event(enable_timing=True))
+                events[(k, f)][0][-1].record(stream)
+            gens[k].generate(steps, f, out=out, stream=stream)
+            if events is not None:
+                events[(k, f)][1].append(torch.cuda.Event(enable_timing=True))
+                events[(k, f)][1][-1].record(stream)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(gpu_selector(torch))
+    clocks.start()
+    time.sleep(0.3)
+    events = {p: ([], []) for p in pairs}
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        one_step(events)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clock_info = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    samples = world * args.steps * len(pairs) * n * steps
+    value = samples / (ms_max * 1e-3) / 1e9
+
+    per_kernel = {}
+    for (k, f), (s_ev, e_ev) in events.items():
+        d = [a.elapsed_time(b) for a, b in zip(s_ev, e_ev)]
+        avg = sum(d) / len(d)
+        b = alg_bytes(k, n, steps)
+        per_kernel[f"{KNAME[k]}_{FNAME[f]}"] = {
+            "ms": avg, "gsamples_s": n * steps / (avg * 1e-3) / 1e9,
+            "gbs": b / (avg * 1e-3) / 1e9, "total_ms": sum(d)}
+    dom = max(per_kernel, key=lambda x: per_kernel[x]["total_ms"])
+    peak, peak_src = peaks()
+    dk = KINDS[[KNAME[k] for k in KINDS].index(dom.split("_")[0])]
+    achieved = alg_bytes(dk, n, steps) / (per_kernel[dom]["ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(dom, workload),
+                "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, "
+                "copy read+write)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": alg_bytes(dk, n, steps)}
+
+    # write-only bandwidth probe over the same buffer (context for the roofline)
+    nbytes = out.numel() * 4
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capi.check(capi.lib().gbrng_probe_write(ctypes.c_void_p(out.data_ptr()), nbytes, sms * 8,
+                                            256, 0, 1, ctypes.c_void_p(stream.cuda_stream)))
+    pe0.record(stream)
+    capi.check(capi.lib().gbrng_probe_write(ctypes.c_void_p(out.data_ptr()), nbytes, sms * 8,
+                                            256, 0, 3, ctypes.c_void_p(stream.cuda_stream)))
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    write_only_gbs = 3 * nbytes / (pe0.elapsed_time(pe1) * 1e-3) / 1e9
+
+    # end to end: the host-delivery call, D2H copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        del out
+        torch.cuda.empty_cache()
+        host = torch.empty((steps, n), dtype=torch.int32, pin_memory=True)
+        for k, f in pairs[:1]:
+            gens[k].generate_host(steps, f, out=host)  # warm-up (staging buffers)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for k, f in pairs:
+                gens[k].generate_host(steps, f, out=host)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dt_t = torch.tensor([dt], device="cuda")
+        if world > 1:
+            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+        dt = float(dt_t.item())
+        e2e_samples = world * args.e2e_steps * len(pairs) * n * steps
+        e2e = {"value": e2e_samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": len(pairs) * n * steps * 4,
+               "steps": args.e2e_steps,
+               "api": "rng_generate_host into pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(steps)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload, "kinds": ["mwc", "xor128", "kiss"],
+                       "fmts": ["u32", "f32"], "n_streams": n, "n_per_stream": steps,
+                       "launches_per_step": len(pairs), "state": "carried across calls",
+                       "l2": "16 GiB output per launch >> 129 MB L2; no flush"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * len(pairs), "clocks": clock_info,
+            "per_kernel": per_kernel, "write_only_probe_gbs": write_only_gbs,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * C-ABI of the GB300 library for the Marsaglia generators of Hissoiny,
+ * Despres and Ozell, "Using graphics processing units to generate random
+ * numbers" (arXiv:1101.1846): many independent generator streams, each with
+ * its own parameters and seeds (Sec. "Parallelizing RNGs", parametrisation),
+ * writing uint32 or single-precision uniforms to device memory (Sec.
+ * "Performance evaluation").
+ *
+ * Generators (kind):
+ *   RNG_MWC32  multiply-with-carry, base 2^32 (Eq. 2-3):
+ *              t = a*x + c (64-bit); x' = t mod 2^32; c' = t >> 32; out = x'.
+ *              Stream s has multiplier a = the (s+1)-th largest a < 2^32 with
+ *              a*2^32 - 1 a safe prime (background MWC section).
+ *   RNG_XOR128 Marsaglia's xor128 XorShift (4 x 32-bit words; the paper's
+ *              XorShift reference, Marsaglia 2003): t = x ^ (x << 11);
+ *              (x, y, z) = (y, z, w); w = w ^ (w >> 19) ^ t ^ (t >> 8); out = w.
+ *   RNG_KISS   KISS (Sec. "KISS"): one MWC32 step (as above), one xorshift32
+ *              step y ^= y<<13; y ^= y>>17; y ^= y<<5 (Eq. 6) and one LCG
+ *              step z = 69069 z + 1234567 mod 2^32 (Eq. 7); out is the sum
+ *              of the three new values mod 2^32.
+ * Formats (fmt):
+ *   RNG_U32    the 32-bit output.
+ *   RNG_F32    (float)(u >> 8) * 2^-24, exactly; in [0, 1 - 2^-24]
+ *              (the uniform variant of Sec. "Performance evaluation").
+ *
+ * Seeding: stream s of a generator created with `seed` draws from
+ * splitmix64 started at seed + s (mod 2^64): MWC (x, c) = (lo32, hi32 mod a)
+ * of a draw, redrawn while (x, c) is (0, 0) or (2^32 - 1, a - 1); xor128
+ * words = lo32, hi32 of two draws, redrawn while all zero; KISS (x, c) as
+ * MWC, then y = lo32 and z = hi32 of the next draw, y redrawn (lo32 of
+ * further draws) while zero.
+ *
+ * Output layout (stream-interleaved): output j (0-based, counted from the
+ * start of the call) of stream s is element out[j * n_streams + s].  Each
+ * call continues every stream where the previous call on the handle left it
+ * (the state is written back after every call, Sec. "Performance
+ * evaluation").
+ *
+ * Conventions for every call:
+ *   - Return 0 (RNG_OK) on success or a negative rng_status.  rng_create
+ *     returns NULL on failure.  The status of the last failing call on the
+ *     calling host thread is kept for rng_last_error().
+ *   - Device work is enqueued on the handle's CUDA stream (default: the
+ *     legacy default stream; see rng_set_stream) and the call returns
+ *     without waiting, except where a call says it synchronises.
+ *   - A failed call leaves the generator state unchanged, except after
+ *     RNG_ERR_CUDA from an already-launched kernel (the CUDA context is then
+ *     in an error state).
+ *   - A handle is not thread-safe: use each one from one host thread at a
+ *     time.  Different handles are independent.
+ *   - The device is the one current on the calling thread at rng_create;
+ *     later calls on the handle make it current themselves.
+ */
+#ifndef GBRNG_RNG_H
+#define GBRNG_RNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rng_gen *rng_handle;
+
+enum rng_kind { RNG_MWC32 = 0, RNG_XOR128 = 1, RNG_KISS = 2 };
+enum rng_fmt { RNG_U32 = 0, RNG_F32 = 1 };
+
+enum rng_status {
+    RNG_OK = 0,
+    RNG_ERR_ARG = -1,     /* invalid argument (kind, fmt, size, pointer)    */
+    RNG_ERR_OOM = -2,     /* device or host allocation failed               */
+    RNG_ERR_CUDA = -3,    /* a CUDA runtime call or kernel launch failed    */
+    RNG_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up             */
+    RNG_ERR_BUSY = -5,    /* admission refused: over the stated budget      */
+    RNG_ERR_NODEV = -6    /* no CUDA device, or not an sm_103 device        */
+};
+
+/* Largest stream count of an MWC32 or KISS generator: the size of the
+ * multiplier table (valid multipliers exist for about 5.6 million a < 2^32;
+ * this bound keeps the device search to a = 1.05e9 and above). */
+#define RNG_MAX_STREAMS_MWC ((uint64_t)1 << 22)
+/* Largest stream count of an xor128 generator (no multiplier table). */
+#define RNG_MAX_STREAMS_XOR ((uint64_t)1 << 30)
+
+/* Creates a generator of `kind` with n_streams independent streams seeded
+ * from `seed` (header comment).  Allocates the per-stream state (and, for
+ * MWC32/KISS, the stream multipliers) on the current device, builds the
+ * device multiplier table if it is not yet long enough (once per device and
+ * process; synchronises), and seeds every stream on the device.  Returns
+ * NULL with rng_last_error() = RNG_ERR_ARG for a bad kind or n_streams of 0
+ * or above the kind's maximum, RNG_ERR_OOM, RNG_ERR_CUDA or RNG_ERR_NODEV.
+ * Paper: per-thread multipliers and seeds (MWC and KISS kernel sections;
+ * Sec. "Parallelizing RNGs"). */
+rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed);
+
+/* Releases the handle and its device memory (waits for its stream first).
+ * NULL is ignored. */
+void rng_destroy(rng_handle h);
+
+/* Makes the handle enqueue its work on `cuda_stream` (a cudaStream_t; NULL
+ * = the legacy default stream).  The caller keeps ownership of the stream
+ * and must not destroy it while work of the handle is pending. */
+int rng_set_stream(rng_handle h, void *cuda_stream);
+
+/* Number of streams and of 32-bit state words per stream (2 for MWC32,
+ * 4 for xor128 and KISS). */
+uint64_t rng_n_streams(rng_handle h);
+int rng_state_words(rng_handle h);
+
+/* The hot path.  Advances every stream n_per_stream times and writes the
+ * outputs, stream-interleaved (header comment), to `out`: a DEVICE pointer,
+ * caller-owned, with room for n_streams * n_per_stream 4-byte elements,
+ * 4-byte aligned (16-byte alignment and n_streams % 4 == 0 select the
+ * vector-store kernel; anything else uses a scalar-store kernel with the
+ * same results).  fmt is RNG_U32 or RNG_F32.  n_per_stream = 0 does
+ * nothing and returns RNG_OK.  Asynchronous on the handle's stream.
+ * Errors: RNG_ERR_ARG (NULL handle or out, bad fmt, misaligned out),
+ * RNG_ERR_CUDA (launch failure).
+ * Paper: the generation kernels of Sec. "GPU implementations" (MWC, XorShift
+ * registers variant, KISS) and the uniform variant of Sec. "Performance
+ * evaluation". */
+int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int fmt);
+
+/* Same outputs as rng_generate, delivered to HOST memory: `host_out` has
+ * room for n_streams * n_per_stream 4-byte elements in the same layout.
+ * The library generates blocks of rows into its own device staging buffers
+ * (allocated on first use, kept with the handle) and copies each block to
+ * the host while the next is generated.  Page-locked host memory is
+ * copied asynchronously; pageable memory works but is slower.  SYNCHRONISES
+ * the handle's stream before returning.  Errors as rng_generate, plus
+ * RNG_ERR_OOM for the staging buffers.
+ * Paper: the generated numbers stay in device memory for later kernels or
+ * are copied to host memory afterwards (Sec. "Performance evaluation"). */
+int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host_out,
+                      int fmt);
+
+/* Copies the state to/from HOST memory: word w of stream s at
+ * buf[w * n_streams + s] (uint32), rng_state_words(h) words per stream, so
+ * `bytes` must be exactly 4 * words * n_streams.  Both synchronise the
+ * handle's stream.  rng_set_state rejects (RNG_ERR_ARG, state unchanged) an
+ * MWC or KISS state whose carry is not below its multiplier or that is an
+ * MWC fixed point, an all-zero xor128 state and a zero KISS xorshift word.
+ * Paper: the state is written back to global memory after each call so that
+ * the sequence can continue (Sec. "Performance evaluation"). */
+int rng_get_state(rng_handle h, void *host_buf, size_t bytes);
+int rng_set_state(rng_handle h, const void *host_buf, size_t bytes);
+
+/* Writes the first k stream multipliers (the MWC32/KISS table: a < 2^32,
+ * largest first, a*2^32 - 1 a safe prime) to `dev_out` (DEVICE pointer,
+ * caller-owned, k uint32).  Builds the table on the current device if it is
+ * not yet long enough; SYNCHRONISES the device.  k <= RNG_MAX_STREAMS_MWC.
+ * Paper: the multiplier condition of the background MWC section. */
+int rng_multipliers(uint64_t k, uint32_t *dev_out);
+
+/* One entry of a batched launch: generator h writes n_per_stream outputs
+ * per stream to the DEVICE pointer out (stream-interleaved, as
+ * rng_generate) in format fmt. */
+typedef struct rng_batch_item {
+    rng_handle h;
+    uint64_t n_per_stream;
+    void *out;
+    int fmt;
+} rng_batch_item;
+
+typedef struct rng_plan *rng_plan_handle;
+
+/* Builds a batched launch over many generators of mixed kinds, stream
+ * counts, lengths and formats: the streams of every item are cut into tiles
+ * of 4 * threads streams (vector-store items: n_streams % 4 == 0 and 16-byte
+ * aligned out) or `threads` streams (other items), the tiles are ordered by
+ * length, largest first, and the work list is copied to the device
+ * (synchronises).  threads = CTA size (power of two, 32..512; 0 = 128),
+ * ctas_per_sm = resident CTAs the persistent grid puts on each SM (1..32;
+ * 0 = as many as fit).  Each handle may appear at most once; items with
+ * n_per_stream = 0 are skipped.  The plan refers to the handles' device
+ * memory and the out pointers: it must not outlive them.  Returns NULL with
+ * rng_last_error() = RNG_ERR_ARG (bad item, duplicate handle, handles on
+ * different devices), RNG_ERR_OOM or RNG_ERR_CUDA.
+ * Paper: none; the parametrised streams of Sec. "Parallelizing RNGs" served
+ * as one launch. */
+rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n_items,
+                                int threads, int ctas_per_sm);
+
+/* Enqueues the plan on `cuda_stream`: a counter reset and ONE persistent
+ * kernel whose CTAs take tiles from the work list through an atomic counter
+ * (no device-side waits).  Outputs and state afterwards are bit-identical to
+ * calling rng_generate on each item in turn; launching again continues every
+ * stream, like a second rng_generate.  No host synchronisation, so the call
+ * can be captured in a CUDA graph and replayed.  Two launches of the same
+ * plan must not overlap on the device. */
+int rng_plan_launch(rng_plan_handle p, void *cuda_stream);
+
+/* Tiles in the plan, and its CTA size and persistent grid size. */
+uint64_t rng_plan_tiles(rng_plan_handle p);
+int rng_plan_shape(rng_plan_handle p, int *threads, int *grid);
+
+/* Frees the plan (waits for its device work first).  NULL is ignored. */
+void rng_plan_destroy(rng_plan_handle p);
+
+/* Convenience: create a plan with the default shape, launch it on
+ * `cuda_stream`, wait for it, and free it.  SYNCHRONISES. */
+int rng_generate_batch(const rng_batch_item *items, size_t n_items,
+                       void *cuda_stream);
+
+/* Status of the last failing call on this host thread (RNG_OK if none);
+ * and a static description of a status code. */
+int rng_last_error(void);
+const char *rng_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBRNG_RNG_H */

@@ -1,0 +1,46 @@
+/*
+ * Launch-shape and measurement entry points of the GB300 generator library
+ * (companions of rng.h used by the autotuner and the benchmark).  The paper
+ * tunes the block size (128/256/512 threads, occupancy-calculator choice in
+ * the MWC and XorShift kernel sections) and measures the achievable memory
+ * bandwidth with a separate benchmark (Sec. "Discussion"); these are the
+ * GB300 counterparts.
+ */
+#ifndef GBRNG_RNG_TUNE_H
+#define GBRNG_RNG_TUNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Launch shape of the vector-store generate kernel for (kind, fmt):
+ * v = groups of four streams per thread (1 or 2), block = threads per CTA
+ * (power of two, 32..512), hint = 1 for streaming (evict-first) stores,
+ * 0 for default stores.  Applies to later rng_generate calls in this process
+ * on every device; does not change any output.  Returns 0 or RNG_ERR_ARG. */
+int gbrng_set_launch(int kind, int fmt, int v, int block, int hint);
+int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
+
+/* Write-only bandwidth probe: fills `bytes` (a multiple of 16) of the DEVICE
+ * buffer `dst` with 16-byte stores from a grid of `blocks` x `threads`
+ * (grid-stride), on `cuda_stream`, `reps` times back to back.  hint as
+ * above.  Asynchronous.  The paper measured its card's achievable bandwidth
+ * the same way, with writes only (Sec. "Discussion"). */
+int gbrng_probe_write(void *dst, uint64_t bytes, int blocks, int threads, int hint,
+                      int reps, void *cuda_stream);
+
+/* Integer-pipe probe: every thread runs `iters` dependent-free iterations of
+ * `op` on 8 independent chains (op 0 = 32x32->64 multiply-add as in one MWC
+ * step, op 1 = 32-bit multiply-add as in the LCG, op 2 = shift+xor as in a
+ * xorshift step, op 3 = 32-bit add) and writes one word per thread to `sink`
+ * (DEVICE, blocks*threads uint32).  Asynchronous.  Used to measure the
+ * integer throughput the generators can reach (the paper's U_ops, Eq. 9). */
+int gbrng_probe_int(int op, uint32_t *sink, int blocks, int threads, uint64_t iters,
+                    void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBRNG_RNG_TUNE_H */

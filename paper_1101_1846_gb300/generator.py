@@ -1,0 +1,177 @@
+"""Python face of the library: PyTorch supplies device memory and streams,
+every sample is made by the CUDA kernels behind the C-ABI (capi.py)."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import capi
+
+
+def _stream_ptr(stream: torch.cuda.Stream | None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dtype(fmt: int) -> torch.dtype:
+    return torch.int32 if fmt == capi.RNG_U32 else torch.float32
+
+
+class Generator:
+    """n_streams parallel streams of one generator kind on the current
+    device.  generate() returns a tensor of shape (n_per_stream, n_streams):
+    row j holds output j of every stream (the stream-interleaved layout).
+    uint32 outputs are returned in an int32 tensor (same bits)."""
+
+    def __init__(self, kind: int | str, n_streams: int, seed: int):
+        kind = capi.KINDS.get(kind, kind) if isinstance(kind, str) else kind
+        h = capi.lib().rng_create(int(kind), int(n_streams), int(seed) & (2**64 - 1))
+        if not h:
+            raise capi.RngError(capi.lib().rng_last_error(), "rng_create")
+        self.h = h
+        self.kind = int(kind)
+        self.n_streams = int(n_streams)
+        self.seed = int(seed)
+        self.words = capi.lib().rng_state_words(h)
+        self.device = torch.cuda.current_device()
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            capi.lib().rng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _bind(self, stream) -> None:
+        capi.check(capi.lib().rng_set_stream(self.h, ctypes.c_void_p(_stream_ptr(stream))),
+                   "rng_set_stream")
+
+    def generate(self, n_per_stream: int, fmt: int | str = capi.RNG_U32,
+                 out: torch.Tensor | None = None,
+                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        fmt = capi.FMTS.get(fmt, fmt) if isinstance(fmt, str) else fmt
+        if out is None:
+            out = torch.empty((n_per_stream, self.n_streams), dtype=_dtype(fmt),
+                              device=f"cuda:{self.device}")
+        assert out.is_cuda and out.is_contiguous() and out.element_size() == 4
+        assert out.numel() >= n_per_stream * self.n_streams
+        self._bind(stream)
+        capi.check(capi.lib().rng_generate(self.h, n_per_stream,
+                                           ctypes.c_void_p(out.data_ptr()), fmt),
+                   "rng_generate")
+        return out
+
+    def generate_host(self, n_per_stream: int, fmt: int | str = capi.RNG_U32,
+                      out: torch.Tensor | None = None,
+                      stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        """Same outputs delivered to (pinned) host memory; synchronises."""
+        fmt = capi.FMTS.get(fmt, fmt) if isinstance(fmt, str) else fmt
+        if out is None:
+            out = torch.empty((n_per_stream, self.n_streams), dtype=_dtype(fmt),
+                              pin_memory=True)
+        assert not out.is_cuda and out.is_contiguous()
+        assert out.numel() >= n_per_stream * self.n_streams
+        self._bind(stream)
+        capi.check(capi.lib().rng_generate_host(self.h, n_per_stream,
+                                                ctypes.c_void_p(out.data_ptr()), fmt),
+                   "rng_generate_host")
+        return out
+
+    def get_state(self) -> torch.Tensor:
+        """State words as an int32 tensor (words, n_streams) on the host."""
+        buf = torch.empty((self.words, self.n_streams), dtype=torch.int32)
+        capi.check(capi.lib().rng_get_state(self.h, ctypes.c_void_p(buf.data_ptr()),
+                                            buf.numel() * 4), "rng_get_state")
+        return buf
+
+    def set_state(self, state: torch.Tensor) -> None:
+        buf = state.to(torch.int32).contiguous().cpu()
+        capi.check(capi.lib().rng_set_state(self.h, ctypes.c_void_p(buf.data_ptr()),
+                                            buf.numel() * 4), "rng_set_state")
+
+
+def multipliers(k: int, device: int | None = None) -> torch.Tensor:
+    """The first k MWC multipliers from the device table (int32 bits)."""
+    dev = torch.cuda.current_device() if device is None else device
+    out = torch.empty(k, dtype=torch.int32, device=f"cuda:{dev}")
+    with torch.cuda.device(dev):
+        capi.check(capi.lib().rng_multipliers(k, ctypes.c_void_p(out.data_ptr())),
+                   "rng_multipliers")
+    return out
+
+
+@dataclass
+class BatchItem:
+    gen: Generator
+    n_per_stream: int
+    out: torch.Tensor
+    fmt: int
+
+
+def _items(items: list[BatchItem]):
+    arr = (capi.rng_batch_item * len(items))()
+    for i, it in enumerate(items):
+        assert it.out.is_cuda and it.out.is_contiguous()
+        assert it.out.numel() >= it.n_per_stream * it.gen.n_streams
+        arr[i].h = it.gen.h
+        arr[i].n_per_stream = it.n_per_stream
+        arr[i].out = it.out.data_ptr()
+        arr[i].fmt = it.fmt
+    return arr
+
+
+class Plan:
+    """A batched launch over many generators (rng_plan_*).  launch() enqueues
+    one persistent kernel and can be captured in a CUDA graph."""
+
+    def __init__(self, items: list[BatchItem], threads: int = 0, ctas_per_sm: int = 0):
+        self._keep = items  # the plan refers to these tensors and handles
+        arr = _items(items)
+        p = capi.lib().rng_plan_create(arr, len(items), threads, ctas_per_sm)
+        if not p:
+            raise capi.RngError(capi.lib().rng_last_error(), "rng_plan_create")
+        self.p = p
+
+    @property
+    def tiles(self) -> int:
+        return int(capi.lib().rng_plan_tiles(self.p))
+
+    @property
+    def shape(self) -> tuple[int, int]:
+        t, g = ctypes.c_int(), ctypes.c_int()
+        capi.check(capi.lib().rng_plan_shape(self.p, ctypes.byref(t), ctypes.byref(g)))
+        return t.value, g.value
+
+    def launch(self, stream: torch.cuda.Stream | None = None) -> None:
+        capi.check(capi.lib().rng_plan_launch(self.p, ctypes.c_void_p(_stream_ptr(stream))),
+                   "rng_plan_launch")
+
+    def close(self) -> None:
+        if getattr(self, "p", None):
+            capi.lib().rng_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate_batch(items: list[BatchItem], stream: torch.cuda.Stream | None = None) -> None:
+    arr = _items(items)
+    capi.check(capi.lib().rng_generate_batch(arr, len(items),
+                                             ctypes.c_void_p(_stream_ptr(stream))),
+               "rng_generate_batch")

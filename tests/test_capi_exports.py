@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every function declared in
+include/*.h; host-side argument checks work without a GPU."""
+from __future__ import annotations
+
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_1101_1846_gb300 import build, capi
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions() -> set[str]:
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof"):
+                names.add(name)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.lib()
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for must in ("rng_create", "rng_generate", "rng_destroy", "rng_generate_host",
+                 "rng_get_state", "rng_set_state", "rng_plan_create", "rng_plan_launch",
+                 "rng_generate_batch", "rng_multipliers", "rng_last_error",
+                 "rng_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(declared_functions()):
+        assert hasattr(lib, name), name
+    assert set(capi.SIGNATURES) == declared_functions()
+
+
+def test_strerror_covers_statuses(lib):
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert lib.rng_strerror(s) not in (None, b"unknown status")
+    assert lib.rng_strerror(-99) == b"unknown status"
+
+
+def test_argument_checks_need_no_gpu(lib):
+    # invalid kind / zero or oversized stream counts are rejected first
+    assert lib.rng_create(7, 16, 1) is None
+    assert lib.rng_last_error() == capi.RNG_ERR_ARG
+    assert lib.rng_create(0, 0, 1) is None
+    assert lib.rng_last_error() == capi.RNG_ERR_ARG
+    assert lib.rng_create(2, capi.RNG_MAX_STREAMS_MWC + 1, 1) is None
+    assert lib.rng_last_error() == capi.RNG_ERR_ARG
+    assert lib.rng_generate(None, 4, None, 0) == capi.RNG_ERR_ARG
+    assert lib.rng_get_state(None, None, 0) == capi.RNG_ERR_ARG
+    assert lib.rng_plan_create(None, 0, 0, 0) is None
+    assert lib.gbrng_set_launch(0, 0, 3, 256, 0) == capi.RNG_ERR_ARG
+    assert lib.gbrng_set_launch(0, 0, 1, 100, 0) == capi.RNG_ERR_ARG
+    lib.rng_destroy(None)
+    lib.rng_plan_destroy(None)
+
+
+def test_launch_shape_roundtrip(lib):
+    v, b, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lib.gbrng_get_launch(2, 1, ctypes.byref(v), ctypes.byref(b), ctypes.byref(h)) == 0
+    old = (v.value, b.value, h.value)
+    assert lib.gbrng_set_launch(2, 1, 2, 128, 1) == 0
+    lib.gbrng_get_launch(2, 1, ctypes.byref(v), ctypes.byref(b), ctypes.byref(h))
+    assert (v.value, b.value, h.value) == (2, 128, 1)
+    assert lib.gbrng_set_launch(2, 1, *old) == 0
+
+
+def test_no_device_reports_nodev(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert lib.rng_create(0, 16, 1) is None
+    assert lib.rng_last_error() == capi.RNG_ERR_NODEV
