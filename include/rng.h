@@ -203,6 +203,28 @@ void rng_plan_destroy(rng_plan_handle p);
 int rng_generate_batch(const rng_batch_item *items, size_t n_items,
                        void *cuda_stream);
 
+/* Allocation-free variant of rng_generate_batch, for callers that cannot
+ * allocate device memory when they need samples: an application whose own
+ * pool allocator holds the whole device budget, or a latency-sensitive loop
+ * that must not pay for, or be synchronised by, cudaMalloc and cudaFree.
+ * Same outputs and state afterwards as rng_generate_batch on the same items
+ * (same work list and kernel, CTA size 128).  The work list and its tile
+ * counter live in one fixed device array inside the library, of 256 bytes
+ * plus 32768 tiles (about 1.8 MB, held by every GPU that loads the library
+ * until the process exits): a call may cover at most 4096 items and 32768
+ * tiles (a tile is 512 streams of an item with n_streams % 4 == 0 and a
+ * 16-byte aligned out, else 128 streams); more returns RNG_ERR_ARG and
+ * launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  The first call on a device looks up the device address of that
+ * array (once per device), so make the first call before any stream capture.
+ * Asynchronous on `cuda_stream`: the work list is copied from library host
+ * memory before the call returns.  Every call shares the one array, which
+ * keeps the last call's contents; calls whose kernels overlap on the GPU
+ * race and give wrong results, so order them on one stream or with events.
+ * Errors as rng_generate_batch.  The paper has no counterpart. */
+int rng_generate_batch_noalloc(const rng_batch_item *items, size_t n_items,
+                               void *cuda_stream);
+
 /* Status of the last failing call on this host thread (RNG_OK if none);
  * and a static description of a status code. */
 int rng_last_error(void);

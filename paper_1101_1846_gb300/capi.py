@@ -50,6 +50,8 @@ SIGNATURES = {
     "rng_plan_destroy": (None, [ctypes.c_void_p]),
     "rng_generate_batch": (ctypes.c_int, [ctypes.POINTER(rng_batch_item), ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "rng_generate_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(rng_batch_item),
+                                                  ctypes.c_size_t, ctypes.c_void_p]),
     "rng_last_error": (ctypes.c_int, []),
     "rng_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gbrng_set_launch": (ctypes.c_int, [ctypes.c_int] * 5),

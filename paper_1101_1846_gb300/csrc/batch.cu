@@ -254,3 +254,142 @@ extern "C" int rng_generate_batch(const rng_batch_item *items, size_t n_items, v
         st = cuda_status(e);
     return st;
 }
+
+// ------------------------------------------------------------------------
+// Allocation-free batched launch.  Same work list and the same persistent
+// kernel as the plan path above, but the work list and the tile counter live
+// in one fixed, file-scope device array instead of memory from cudaMalloc,
+// and the host side builds the list in a fixed host array, so a call makes
+// no device or host heap allocation.  Some callers cannot allocate device
+// memory at the point where they need random numbers: an application whose
+// pool allocator owns the whole device budget, or a latency-sensitive loop
+// that must not pay for (or be synchronised by) a cudaMalloc/cudaFree pair.
+// The paper has no counterpart of this entry point.
+// ------------------------------------------------------------------------
+#include <mutex>
+
+namespace gbrng {
+namespace {
+
+constexpr uint64_t kNoAllocMaxTiles = 32768;  // work-list capacity, in tiles
+constexpr size_t kNoAllocMaxItems = 4096;     // items per call
+constexpr size_t kNoAllocHeader = 256;        // tile counter, then padding
+constexpr size_t kNoAllocBytes = kNoAllocHeader + kNoAllocMaxTiles * sizeof(Unit);
+
+// The scratch: bytes [0, 8) hold the tile counter, the work list starts at
+// byte kNoAllocHeader.  Every GPU that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;                      // guards the host arrays below
+void *g_noalloc_dev_ptr[64] = {nullptr};         // device address of the scratch
+Unit g_noalloc_host_units[kNoAllocMaxTiles];     // host copy of the work list
+const void *g_noalloc_handles[kNoAllocMaxItems]; // duplicate check
+
+}  // namespace
+}  // namespace gbrng
+
+extern "C" int rng_generate_batch_noalloc(const rng_batch_item *items, size_t n_items,
+                                          void *cuda_stream)
+{
+    if (!items || n_items == 0 || n_items > kNoAllocMaxItems)
+        return set_error(RNG_ERR_ARG);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    int device = -1;
+    for (size_t i = 0; i < n_items; ++i) {
+        Gen *g = reinterpret_cast<Gen *>(items[i].h);
+        if (!g || (items[i].fmt != RNG_U32 && items[i].fmt != RNG_F32))
+            return set_error(RNG_ERR_ARG);
+        if (device < 0)
+            device = g->device;
+        if (g->device != device || device >= 64)
+            return set_error(RNG_ERR_ARG);
+        g_noalloc_handles[i] = g;
+    }
+    std::sort(g_noalloc_handles, g_noalloc_handles + n_items);
+    for (size_t i = 1; i < n_items; ++i)
+        if (g_noalloc_handles[i] == g_noalloc_handles[i - 1])
+            return set_error(RNG_ERR_ARG);
+
+    // Work list, as rng_plan_create with its default CTA size builds it.
+    const int threads = 128;
+    uint64_t n_units = 0;
+    for (size_t i = 0; i < n_items; ++i) {
+        const rng_batch_item &it = items[i];
+        Gen *g = reinterpret_cast<Gen *>(it.h);
+        if (it.n_per_stream == 0)
+            continue;
+        if (!it.out || (uintptr_t)it.out % 4 != 0 || it.n_per_stream > UINT64_MAX / 4 / g->n)
+            return set_error(RNG_ERR_ARG);
+        bool vec = g->n % 4 == 0 && (uintptr_t)it.out % 16 == 0;
+        uint64_t tile = vec ? 4ull * threads : (uint64_t)threads;
+        uint64_t tiles = (g->n + tile - 1) / tile;
+        if (n_units + tiles > kNoAllocMaxTiles)
+            return set_error(RNG_ERR_ARG);  // beyond the work-list capacity
+        uint32_t code = (uint32_t)g->kind | ((uint32_t)it.fmt << 2) | (vec ? 8u : 0u);
+        for (uint64_t s0 = 0; s0 < g->n; s0 += tile) {
+            Unit &u = g_noalloc_host_units[n_units++];
+            u = Unit{};
+            u.state = g->d_state;
+            u.a = g->d_a;
+            u.out = static_cast<uint32_t *>(it.out);
+            u.n = g->n;
+            u.steps = it.n_per_stream;
+            u.s0 = (uint32_t)s0;
+            u.count = (uint32_t)std::min<uint64_t>(tile, g->n - s0);
+            u.code = code;
+        }
+    }
+    if (n_units == 0)
+        return RNG_OK;
+    // Longest tiles first; ties ordered by generator and first stream (an
+    // in-place sort, no buffer; the order only affects scheduling).
+    std::sort(g_noalloc_host_units, g_noalloc_host_units + n_units,
+              [](const Unit &x, const Unit &y) {
+                  if (x.steps != y.steps)
+                      return x.steps > y.steps;
+                  if (x.state != y.state)
+                      return x.state < y.state;
+                  return x.s0 < y.s0;
+              });
+
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess)
+        return set_error(RNG_ERR_CUDA);
+    if (prev != device && cudaSetDevice(device) != cudaSuccess)
+        return set_error(RNG_ERR_CUDA);
+    int st = RNG_OK;
+    // Set-up, once per device with that device current: the device address
+    // of the scratch array (its name in host code is only a host stand-in).
+    if (!g_noalloc_dev_ptr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            st = cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        else
+            g_noalloc_dev_ptr[device] = ptr;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int sms = 0, fit = 0;
+    if (!st)
+        st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    if (!st)
+        st = cuda_status(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<0>, threads, 0));
+    unsigned char *base = static_cast<unsigned char *>(g_noalloc_dev_ptr[device]);
+    unsigned long long *next = reinterpret_cast<unsigned long long *>(base);
+    Unit *units = reinterpret_cast<Unit *>(base + kNoAllocHeader);
+    // The copy is from pageable memory: it is staged before the call returns,
+    // so the host array may be reused by the next call.
+    if (!st)
+        st = cuda_status(cudaMemcpyAsync(units, g_noalloc_host_units, n_units * sizeof(Unit),
+                                         cudaMemcpyHostToDevice, stream));
+    if (!st)  // the counter keeps the last call's value: clear it
+        st = cuda_status(cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream));
+    if (!st) {
+        batch_kernel<0><<<sms * std::max(fit, 1), threads, 0, stream>>>(units, n_units, next);
+        st = cuda_status(cudaGetLastError());
+    }
+    if (prev >= 0 && prev != device)
+        cudaSetDevice(prev);
+    return st;
+}
