@@ -47,6 +47,14 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    p.add_argument("--workload", default="full", choices=["full", "batched"])
+    p.add_argument("--instances", type=int, default=10_000)
+    p.add_argument("--wave-gib", type=float, default=24.0)
+    p.add_argument("--tune", action="store_true", help="autotune launch shapes first")
+    p.add_argument("--ring", type=int, default=3, help="batched: waves in flight")
+    p.add_argument("--no-verify", action="store_true", help="batched: skip the check pass")
+    p.add_argument("--chunk-rows", type=int, default=2048,
+                   help="batched: rows per piece (0 = whole instances)")
     return p.parse_args()
 
 
@@ -367,10 +375,155 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- batched
+def run_batched(args):
+    """10,000 mixed instances (workloads.batched_instances).  Instances are
+    cut into pieces of at most --chunk-rows rows (the state carries from
+    piece to piece, so the pieces give exactly the rows of one call), and
+    the pieces are packed into waves of at most --wave-gib of output
+    (scheduler.chunked_waves).  Every wave is one plan (one persistent
+    kernel) captured in a CUDA graph; waves run on a ring of --ring streams
+    and buffers.  The same instances then run as plain per-instance
+    launches (timed), and a separate untimed pass checks every piece of
+    every wave bit for bit against plain calls."""
+    import torch
+
+    from paper_1101_1846_gb300 import autotune, capi, scheduler, workloads
+    from paper_1101_1846_gb300.generator import BatchItem, Generator, Plan
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    capi.lib()
+    inst = workloads.batched_instances(args.instances, 1234)
+    budget = int(args.wave_gib * (1 << 30))
+    waves = scheduler.chunked_waves([i.n_streams for i in inst],
+                                    [i.n_per_stream for i in inst], budget, args.chunk_rows)
+    R = max(2, args.ring)
+    main = torch.cuda.current_stream()
+    # Consecutive waves hold consecutive pieces of the same instances, so the
+    # waves run in order on one stream; the R buffers only alternate.
+    streams = [torch.cuda.Stream()]
+    longest = max(4 * i.n_streams * i.n_per_stream for i in inst)
+    cap = max(budget, longest) // 4 + 4 * max(len(w) for w in waves)
+    bufs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(R)]
+
+    def carve(buf, wave):
+        outs, off = [], 0
+        for p in wave:
+            m = inst[p.inst].n_streams * p.rows
+            outs.append(buf[off:off + m])
+            off += (m + 3) // 4 * 4  # 16-byte aligned starts
+        return outs
+
+    def make_gens():
+        return [Generator(i.kind, i.n_streams, i.seed) for i in inst]
+
+    def items_for(gens, wave, outs):
+        return [BatchItem(gens[p.inst], p.rows, o, inst[p.inst].fmt) for p, o in zip(wave, outs)]
+
+    t0 = time.perf_counter()
+    gb = make_gens()
+    create_s = time.perf_counter() - t0
+
+    shape, tune_ms = (0, 0), None
+    if args.tune:
+        tg = make_gens()
+        shape, tune_ms = autotune.tune_plan(items_for(tg, waves[0], carve(bufs[0], waves[0])))
+        for g in tg:
+            g.close()
+
+    # plans and graphs for every wave, built before the timed region
+    plans, graphs, tiles = [], [], 0
+    for k, w in enumerate(waves):
+        plan = Plan(items_for(gb, w, carve(bufs[k % R], w)), threads=shape[0],
+                    ctas_per_sm=shape[1])
+        tiles += plan.tiles
+        s = streams[0]
+        s.wait_stream(main)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            plan.launch(s)
+        plans.append(plan)
+        graphs.append(graph)
+    torch.cuda.synchronize()
+
+    samples = sum(i.n_streams * i.n_per_stream for i in inst)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for s in streams:
+        s.wait_stream(main)
+    with torch.cuda.stream(streams[0]):
+        for graph in graphs:
+            graph.replay()
+    for s in streams:
+        main.wait_stream(s)
+    e1.record(main)
+    torch.cuda.synchronize()
+    b_ms = e0.elapsed_time(e1)
+    for plan in plans:
+        plan.close()
+    del graphs
+
+    # plain per-instance launches (one call per instance, one stream)
+    gp = make_gens()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(main)
+    for i, ins in enumerate(inst):
+        gp[i].generate(ins.n_per_stream, ins.fmt, out=bufs[i % R], stream=main)
+    p1.record(main)
+    torch.cuda.synchronize()
+    p_ms = p0.elapsed_time(p1)
+    states_equal = all(torch.equal(a.get_state(), b.get_state()) for a, b in
+                       zip(gb[::41], gp[::41]))
+    for g in gb + gp:
+        g.close()
+
+    # untimed check: every piece of every wave against plain calls
+    mismatched, checked = 0, 0
+    if not args.no_verify:
+        vb, vp = make_gens(), make_gens()
+        for w in waves:
+            ob, op = carve(bufs[0], w), carve(bufs[1], w)
+            plan = Plan(items_for(vb, w, ob), threads=shape[0], ctas_per_sm=shape[1])
+            plan.launch(main)
+            for p, o in zip(w, op):
+                vp[p.inst].generate(p.rows, inst[p.inst].fmt, out=o, stream=main)
+            torch.cuda.synchronize()
+            for x, y in zip(ob, op):
+                checked += 1
+                if not torch.equal(x, y):
+                    mismatched += 1
+            plan.close()
+        states_equal = states_equal and all(
+            torch.equal(a.get_state(), b.get_state()) for a, b in zip(vb, vp))
+        for g in vb + vp:
+            g.close()
+
+    line = {
+        "metric": METRIC, "workload": f"batched_{args.instances}", "impl": "ours",
+        "value": samples / (b_ms * 1e-3) / 1e9, "unit": UNIT,
+        "plain_per_instance_value": samples / (p_ms * 1e-3) / 1e9,
+        "batched_over_plain_per_instance": p_ms / b_ms, "samples": samples,
+        "bytes": 4 * samples, "waves": len(waves), "pieces": sum(len(w) for w in waves),
+        "ring": R, "tiles": tiles, "chunk_rows": args.chunk_rows,
+        "batched_ms": b_ms, "plain_ms": p_ms, "plain_launches": len(inst),
+        "gpu_launches": len(waves), "plan_shape": list(shape), "tune_ms":
+            {f"{t}x{c}": v for (t, c), v in tune_ms.items()} if tune_ms else None,
+        "bit_identical": (mismatched == 0 and states_equal) if not args.no_verify else None,
+        "pieces_checked": checked, "mismatched_pieces": mismatched, "create_s": create_s,
+        "realigned_instances": sum(1 for i in inst if i.n_streams % 4),
+        "config": {"workload": "batched", "instances": args.instances, "seed": 1234,
+                   "wave_bytes": budget, "graph": "one CUDA graph per wave",
+                   "order": f"waves in order on one stream, {R} output buffers"},
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

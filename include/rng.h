@@ -111,9 +111,11 @@ int rng_state_words(rng_handle h);
 /* The hot path.  Advances every stream n_per_stream times and writes the
  * outputs, stream-interleaved (header comment), to `out`: a DEVICE pointer,
  * caller-owned, with room for n_streams * n_per_stream 4-byte elements,
- * 4-byte aligned (16-byte alignment and n_streams % 4 == 0 select the
- * vector-store kernel; anything else uses a scalar-store kernel with the
- * same results).  fmt is RNG_U32 or RNG_F32.  n_per_stream = 0 does
+ * 4-byte aligned.  With n_streams % 4 == 0 and 16-byte alignment every row
+ * is 16-byte aligned; otherwise the rows are realigned in registers and
+ * still written with 16-byte stores, and the last n_streams % 4 streams
+ * use 4-byte stores; the results are the same.  Calls longer than 2^31
+ * steps run as several launches.  fmt is RNG_U32 or RNG_F32.  n_per_stream = 0 does
  * nothing and returns RNG_OK.  Asynchronous on the handle's stream.
  * Errors: RNG_ERR_ARG (NULL handle or out, bad fmt, misaligned out),
  * RNG_ERR_CUDA (launch failure).
@@ -121,6 +123,19 @@ int rng_state_words(rng_handle h);
  * registers variant, KISS) and the uniform variant of Sec. "Performance
  * evaluation". */
 int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int fmt);
+
+/* Advances only streams [s_begin, s_end) (0 <= s_begin < s_end <= n_streams)
+ * n_per_stream times; the other streams keep their state.  Output j of
+ * stream s goes to out[j * ld + (s - s_begin)]: `out` is a DEVICE pointer to
+ * the element of stream s_begin in row 0, 4-byte aligned, and ld >=
+ * s_end - s_begin is the row stride in elements (ld = n_streams and the full
+ * range give rng_generate).  A serving layer uses this to continue a
+ * stream-interleaved sequence from the middle of a row.  Asynchronous.
+ * Errors: RNG_ERR_ARG (bad range, ld or pointer), RNG_ERR_CUDA.
+ * Paper: the per-thread generators of Sec. "Parallelizing RNGs" advanced
+ * independently. */
+int rng_generate_range(rng_handle h, uint64_t s_begin, uint64_t s_end,
+                       uint64_t n_per_stream, void *out, uint64_t ld, int fmt);
 
 /* Same outputs as rng_generate, delivered to HOST memory: `host_out` has
  * room for n_streams * n_per_stream 4-byte elements in the same layout.
@@ -153,30 +168,36 @@ int rng_set_state(rng_handle h, const void *host_buf, size_t bytes);
  * Paper: the multiplier condition of the background MWC section. */
 int rng_multipliers(uint64_t k, uint32_t *dev_out);
 
-/* One entry of a batched launch: generator h writes n_per_stream outputs
- * per stream to the DEVICE pointer out (stream-interleaved, as
- * rng_generate) in format fmt. */
+/* One entry of a batched launch: generator h advances streams
+ * [s_begin, s_end) n_per_stream times and writes output j of stream s to
+ * out[j * ld + (s - s_begin)] (DEVICE pointer, 4-byte aligned) in format
+ * fmt.  s_end = 0 means n_streams, ld = 0 means n_streams; with both 0 and
+ * s_begin = 0 the item is rng_generate(h, n_per_stream, out, fmt). */
 typedef struct rng_batch_item {
     rng_handle h;
     uint64_t n_per_stream;
     void *out;
     int fmt;
+    uint64_t s_begin;
+    uint64_t s_end;
+    uint64_t ld;
 } rng_batch_item;
 
 typedef struct rng_plan *rng_plan_handle;
 
 /* Builds a batched launch over many generators of mixed kinds, stream
  * counts, lengths and formats: the streams of every item are cut into tiles
- * of 4 * threads streams (vector-store items: n_streams % 4 == 0 and 16-byte
- * aligned out) or `threads` streams (other items), the tiles are ordered by
- * length, largest first, and the work list is copied to the device
- * (synchronises).  threads = CTA size (power of two, 32..512; 0 = 128),
+ * of 4 * threads streams when its rows are 16-byte aligned, else of
+ * 4 * (31 * threads / 32 + 1) streams (the last (s_end - s_begin) % 4
+ * streams of such an item form a tile of their own), the tiles are ordered by length, largest first, and
+ * the work list is copied to the device (synchronises).  threads = CTA size (power of two, 32..512; 0 = 128),
  * ctas_per_sm = resident CTAs the persistent grid puts on each SM (1..32;
- * 0 = as many as fit).  Each handle may appear at most once; items with
- * n_per_stream = 0 are skipped.  The plan refers to the handles' device
+ * 0 = as many as fit).  Items of the same handle must cover disjoint stream
+ * ranges (they then run side by side); items with n_per_stream = 0 are
+ * skipped.  The plan refers to the handles' device
  * memory and the out pointers: it must not outlive them.  Returns NULL with
  * rng_last_error() = RNG_ERR_ARG (bad item, duplicate handle, handles on
- * different devices), RNG_ERR_OOM or RNG_ERR_CUDA.
+ * different devices, n_per_stream >= 2^32), RNG_ERR_OOM or RNG_ERR_CUDA.
  * Paper: none; the parametrised streams of Sec. "Parallelizing RNGs" served
  * as one launch. */
 rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n_items,
@@ -210,11 +231,11 @@ int rng_generate_batch(const rng_batch_item *items, size_t n_items,
  * Same outputs and state afterwards as rng_generate_batch on the same items
  * (same work list and kernel, CTA size 128).  The work list and its tile
  * counter live in one fixed device array inside the library, of 256 bytes
- * plus 32768 tiles (about 1.8 MB, held by every GPU that loads the library
+ * plus 32768 tiles of 64 bytes (2 MB, held by every GPU that loads the library
  * until the process exits): a call may cover at most 4096 items and 32768
- * tiles (a tile is 512 streams of an item with n_streams % 4 == 0 and a
- * 16-byte aligned out, else 128 streams); more returns RNG_ERR_ARG and
- * launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
+ * tiles (an item of c = s_end - s_begin streams takes ceil(c / 512) tiles
+ * when its rows are 16-byte aligned, else ceil((c - c % 4) / 500) tiles plus
+ * one when c % 4 != 0); more returns RNG_ERR_ARG and launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
  * called.  The first call on a device looks up the device address of that
  * array (once per device), so make the first call before any stream capture.
  * Asynchronous on `cuda_stream`: the work list is copied from library host

@@ -24,7 +24,9 @@ FMTS = {"u32": RNG_U32, "f32": RNG_F32}
 
 class rng_batch_item(ctypes.Structure):
     _fields_ = [("h", ctypes.c_void_p), ("n_per_stream", ctypes.c_uint64),
-                ("out", ctypes.c_void_p), ("fmt", ctypes.c_int)]
+                ("out", ctypes.c_void_p), ("fmt", ctypes.c_int),
+                ("s_begin", ctypes.c_uint64), ("s_end", ctypes.c_uint64),
+                ("ld", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/*.h
@@ -36,6 +38,9 @@ SIGNATURES = {
     "rng_state_words": (ctypes.c_int, [ctypes.c_void_p]),
     "rng_generate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                     ctypes.c_int]),
+    "rng_generate_range": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
+                                          ctypes.c_int]),
     "rng_generate_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
                                          ctypes.c_void_p, ctypes.c_int]),
     "rng_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),

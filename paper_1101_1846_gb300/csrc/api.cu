@@ -176,7 +176,26 @@ extern "C" int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int 
     DeviceGuard dg(g->device);
     if (!dg.ok)
         return set_error(RNG_ERR_CUDA);
-    GenLaunch p{g->d_state, g->d_a, g->n, n_per_stream, out, g->n};
+    GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, n_per_stream, out, g->n};
+    return launch_generate(g->kind, fmt, p, g->stream);
+}
+
+extern "C" int rng_generate_range(rng_handle h, uint64_t s_begin, uint64_t s_end,
+                                  uint64_t n_per_stream, void *out, uint64_t ld, int fmt)
+{
+    Gen *g = reinterpret_cast<Gen *>(h);
+    if (!g || !valid_fmt(fmt) || s_begin >= s_end || s_end > g->n)
+        return set_error(RNG_ERR_ARG);
+    if (n_per_stream == 0)
+        return RNG_OK;
+    const uint64_t count = s_end - s_begin;
+    if (!out || (uintptr_t)out % 4 != 0 || ld < count ||
+        (n_per_stream - 1) > (UINT64_MAX / 4 - count) / ld)
+        return set_error(RNG_ERR_ARG);
+    DeviceGuard dg(g->device);
+    if (!dg.ok)
+        return set_error(RNG_ERR_CUDA);
+    GenLaunch p{g->d_state, g->d_a, g->n, s_begin, s_end, n_per_stream, out, ld};
     return launch_generate(g->kind, fmt, p, g->stream);
 }
 
@@ -231,7 +250,7 @@ extern "C" int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host
         // buffer b is free once its previous copy (chunk - 2) has finished
         if (chunk >= 2)
             st = cuda_status(cudaStreamWaitEvent(g->stream, g->stage_ev[b], 0));
-        GenLaunch p{g->d_state, g->d_a, g->n, m, g->d_stage[b], g->n};
+        GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, m, g->d_stage[b], g->n};
         if (!st)
             st = launch_generate(g->kind, fmt, p, g->stream);
         if (!st)

@@ -1,15 +1,22 @@
 // Batched generation: many generators of mixed kinds, stream counts, lengths
 // and formats in ONE persistent kernel launch.  Every item's streams are cut
 // into tiles; a CTA takes the next tile from a device work list through an
-// atomic counter and runs the same per-thread body as the plain kernels
+// atomic counter and runs the same per-thread bodies as the plain kernels
 // (gen_body.cuh), so outputs and state are bit-identical to plain launches.
 // Tiles are ordered by length, largest first, so that the longest tiles start
 // first and the launch ends evenly.  Nothing waits on the device: a CTA only
 // increments the counter and stops when the list is exhausted.
+//
+// Tiles of an item with n streams and output `out`:
+//   aligned  (n % 4 == 0, out 16-byte aligned): 4*threads streams per tile,
+//            with row barriers unless every row is 32-byte aligned;
+//   shifted  (otherwise) the first n & ~3 streams, 4*(31*threads/32 + 1)
+//            per tile, rows realigned by warp shuffles;
+//   tail     the last n % 4 streams, one tile, one stream per thread.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
-#include <unordered_set>
 #include <vector>
 
 #include "gen_body.cuh"
@@ -17,29 +24,40 @@
 namespace gbrng {
 namespace {
 
+enum TileMode : uint32_t { kTail = 0, kAligned = 1, kShifted = 2, kAlignedSync = 3 };
+
 struct Unit {
     uint32_t *state;     // generator state (SoA, stride n)
     const uint32_t *a;   // multipliers or nullptr
-    uint32_t *out;       // item output, row stride n
-    uint64_t n;          // generator streams
-    uint64_t steps;      // outputs per stream
+    uint32_t *out;       // output element of stream s0 in row 0
+    uint64_t n;          // generator streams (state stride)
+    uint64_t ld;         // output row stride
+    uint64_t steps;      // outputs per stream (< 2^32)
     uint32_t s0;         // first stream of the tile
     uint32_t count;      // streams in the tile
-    uint32_t code;       // kind | fmt << 2 | vec << 3
+    uint32_t code;       // kind | fmt << 2 | mode << 3
     uint32_t pad;
 };
 
 template <int KIND, int FMT, int HINT>
 __device__ __forceinline__ void run_unit(const Unit &u)
 {
-    const uint64_t end = (uint64_t)u.s0 + u.count;
-    if (u.code & 8u) {
-        body_vec<KIND, FMT, 1, HINT>(u.state, u.a, u.n, u.steps, u.out, u.n,
-                                     u.s0 + 4 * (uint64_t)threadIdx.x, 0, end);
+    const uint32_t mode = u.code >> 3;
+    const uint32_t steps = (uint32_t)u.steps;
+    const uint64_t c_first = 4 * (uint64_t)threadIdx.x;
+    if (mode == kAligned) {
+        if (c_first < u.count)
+            body_vec<KIND, FMT, 1, HINT>(u.state, u.a, u.n, steps, u.out + c_first, u.ld,
+                                         u.s0 + c_first, 0);
+    } else if (mode == kAlignedSync) {
+        body_vec_sync<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c_first, u.ld,
+                                       u.s0 + c_first, c_first < u.count);
+    } else if (mode == kShifted) {
+        body_shift<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out, u.ld, u.s0, u.count / 4);
     } else {
-        uint64_t s = u.s0 + (uint64_t)threadIdx.x;
-        if (s < end)
-            body_scalar<KIND, FMT, HINT>(u.state, u.a, u.n, u.steps, u.out, u.n, s);
+        const uint64_t c = threadIdx.x;
+        if (c < u.count)
+            body_scalar<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c, u.ld, u.s0 + c);
     }
 }
 
@@ -69,12 +87,140 @@ batch_kernel(const Unit *__restrict__ units, uint64_t n_units, unsigned long lon
     }
 }
 
+constexpr int kDefaultThreads = 128;
+constexpr int kHint = 1;  // streaming stores, as the plain kernels
+
+// An item's stream range and row stride with the defaults filled in.
+struct ItemRange {
+    uint64_t s_begin, s_end, ld;
+};
+
+ItemRange range_of(const rng_batch_item &it, const Gen *g)
+{
+    ItemRange r{it.s_begin, it.s_end ? it.s_end : g->n, it.ld ? it.ld : g->n};
+    return r;
+}
+
+// A handle and stream range, for the overlap check.
+struct Claim {
+    const void *h;
+    uint64_t s_begin, s_end;
+};
+
+// Checks every item, and that items of the same handle cover disjoint
+// stream ranges; `scratch` has room for n_items claims.  Sets *device to the
+// items' device.
+int validate_items(const rng_batch_item *items, size_t n_items, Claim *scratch, int *device)
+{
+    *device = -1;
+    for (size_t i = 0; i < n_items; ++i) {
+        const rng_batch_item &it = items[i];
+        Gen *g = reinterpret_cast<Gen *>(it.h);
+        if (!g || (it.fmt != RNG_U32 && it.fmt != RNG_F32))
+            return set_error(RNG_ERR_ARG);
+        if (*device < 0)
+            *device = g->device;
+        if (g->device != *device)
+            return set_error(RNG_ERR_ARG);
+        const ItemRange r = range_of(it, g);
+        if (r.s_begin >= r.s_end || r.s_end > g->n || r.ld < r.s_end - r.s_begin)
+            return set_error(RNG_ERR_ARG);
+        if (it.n_per_stream) {
+            const uint64_t count = r.s_end - r.s_begin;
+            if (!it.out || (uintptr_t)it.out % 4 != 0 || it.n_per_stream >= (1ull << 32) ||
+                (it.n_per_stream - 1) > (UINT64_MAX / 4 - count) / r.ld)
+                return set_error(RNG_ERR_ARG);
+        }
+        scratch[i] = Claim{g, r.s_begin, r.s_end};
+    }
+    std::sort(scratch, scratch + n_items, [](const Claim &x, const Claim &y) {
+        return x.h != y.h ? x.h < y.h : x.s_begin < y.s_begin;
+    });
+    for (size_t i = 1; i < n_items; ++i)
+        if (scratch[i].h == scratch[i - 1].h && scratch[i].s_begin < scratch[i - 1].s_end)
+            return set_error(RNG_ERR_ARG);
+    return *device < 0 ? set_error(RNG_ERR_ARG) : RNG_OK;
+}
+
+// Writes the tiles of every item to out[0 .. cap) (out may be null) and
+// returns how many there are.
+uint64_t fill_units(const rng_batch_item *items, size_t n_items, int threads, Unit *out,
+                    uint64_t cap)
+{
+    uint64_t count = 0;
+    for (size_t i = 0; i < n_items; ++i) {
+        const rng_batch_item &it = items[i];
+        Gen *g = reinterpret_cast<Gen *>(it.h);
+        if (it.n_per_stream == 0)
+            continue;
+        const ItemRange r = range_of(it, g);
+        const uint64_t n_item = r.s_end - r.s_begin;
+        uint32_t *base = static_cast<uint32_t *>(it.out);
+        const bool aligned = n_item % 4 == 0 && r.ld % 4 == 0 && (uintptr_t)base % 16 == 0 &&
+                             g->n % 4 == 0 && r.s_begin % 4 == 0;
+        const bool sectors = aligned && r.ld % 8 == 0 && (uintptr_t)base % 32 == 0;
+        const uint32_t amode = sectors ? kAligned : kAlignedSync;
+        const uint64_t main = n_item & ~(uint64_t)3;
+        // aligned tiles: 4 streams per thread; realigned tiles: 31K + 1
+        // groups of four for K warps (one halo lane per warp but the last)
+        const uint64_t tile = aligned ? 4ull * threads : 4ull * (31 * (threads / 32) + 1);
+        auto put = [&](uint64_t c0, uint64_t c, uint32_t mode) {
+            if (out && count < cap) {
+                Unit &u = out[count];
+                u = Unit{};
+                u.state = g->d_state;
+                u.a = g->d_a;
+                u.out = base + c0;
+                u.n = g->n;
+                u.ld = r.ld;
+                u.steps = it.n_per_stream;
+                u.s0 = (uint32_t)(r.s_begin + c0);
+                u.count = (uint32_t)c;
+                u.code = (uint32_t)g->kind | ((uint32_t)it.fmt << 2) | (mode << 3);
+            }
+            ++count;
+        };
+        for (uint64_t c0 = 0; c0 < main; c0 += tile)
+            put(c0, std::min<uint64_t>(tile, main - c0), aligned ? amode : kShifted);
+        if (main < n_item)
+            put(main, n_item - main, kTail);
+    }
+    return count;
+}
+
+// Longest tiles first; ties by generator and first stream, so the order is
+// deterministic (it only affects scheduling).
+void order_units(Unit *u, uint64_t n)
+{
+    std::sort(u, u + n, [](const Unit &x, const Unit &y) {
+        if (x.steps != y.steps)
+            return x.steps > y.steps;
+        if (x.state != y.state)
+            return x.state < y.state;
+        return x.s0 != y.s0 ? x.s0 < y.s0 : x.out < y.out;
+    });
+}
+
+int grid_for(int device, int threads, int ctas_per_sm, int *grid)
+{
+    int sms = 0, fit = 0;
+    int st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    if (!st)
+        st = cuda_status(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<kHint>, threads, 0));
+    if (!st) {
+        fit = std::max(fit, 1);
+        *grid = sms * (ctas_per_sm ? std::min(ctas_per_sm, fit) : fit);
+    }
+    return st;
+}
+
 struct Plan {
     int device = 0;
     Unit *d_units = nullptr;
     uint64_t n_units = 0;
     unsigned long long *d_next = nullptr;
-    int threads = 128;
+    int threads = kDefaultThreads;
     int grid = 0;
 };
 
@@ -100,56 +246,20 @@ extern "C" rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n
         return nullptr;
     }
     if (threads == 0)
-        threads = 128;
+        threads = kDefaultThreads;
     if (threads < 32 || threads > 512 || (threads & (threads - 1)) || ctas_per_sm < 0 ||
         ctas_per_sm > 32) {
         set_error(RNG_ERR_ARG);
         return nullptr;
     }
     int device = -1;
-    std::unordered_set<const void *> seen;
-    std::vector<Unit> units;
-    for (size_t i = 0; i < n_items; ++i) {
-        const rng_batch_item &it = items[i];
-        Gen *g = reinterpret_cast<Gen *>(it.h);
-        if (!g || (it.fmt != RNG_U32 && it.fmt != RNG_F32)) {
-            set_error(RNG_ERR_ARG);
-            return nullptr;
-        }
-        if (device < 0)
-            device = g->device;
-        if (g->device != device || !seen.insert(g).second) {
-            set_error(RNG_ERR_ARG);
-            return nullptr;
-        }
-        if (it.n_per_stream == 0)
-            continue;
-        if (!it.out || (uintptr_t)it.out % 4 != 0 || it.n_per_stream > UINT64_MAX / 4 / g->n) {
-            set_error(RNG_ERR_ARG);
-            return nullptr;
-        }
-        bool vec = g->n % 4 == 0 && (uintptr_t)it.out % 16 == 0;
-        uint64_t tile = vec ? 4ull * threads : (uint64_t)threads;
-        uint32_t code = (uint32_t)g->kind | ((uint32_t)it.fmt << 2) | (vec ? 8u : 0u);
-        for (uint64_t s0 = 0; s0 < g->n; s0 += tile) {
-            Unit u{};
-            u.state = g->d_state;
-            u.a = g->d_a;
-            u.out = static_cast<uint32_t *>(it.out);
-            u.n = g->n;
-            u.steps = it.n_per_stream;
-            u.s0 = (uint32_t)s0;
-            u.count = (uint32_t)std::min<uint64_t>(tile, g->n - s0);
-            u.code = code;
-            units.push_back(u);
-        }
-    }
-    if (device < 0) {
-        set_error(RNG_ERR_ARG);
+    std::vector<Claim> claims(n_items);
+    if (validate_items(items, n_items, claims.data(), &device))
         return nullptr;
-    }
-    std::stable_sort(units.begin(), units.end(),
-                     [](const Unit &x, const Unit &y) { return x.steps > y.steps; });
+    std::vector<Unit> units(fill_units(items, n_items, threads, nullptr, 0));
+    fill_units(items, n_items, threads, units.data(), units.size());
+    order_units(units.data(), units.size());
+
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != device)
@@ -160,15 +270,7 @@ extern "C" rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n
         p->device = device;
         p->threads = threads;
         p->n_units = units.size();
-        int sms = 0, fit = 0;
-        st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-        if (!st)
-            st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &fit, batch_kernel<0>, threads, 0));
-        if (!st) {
-            int per = ctas_per_sm ? std::min(ctas_per_sm, std::max(fit, 1)) : std::max(fit, 1);
-            p->grid = sms * per;
-        }
+        st = grid_for(device, threads, ctas_per_sm, &p->grid);
     }
     if (!st && p->n_units) {
         size_t bytes = p->n_units * sizeof(Unit);
@@ -202,7 +304,7 @@ extern "C" int rng_plan_launch(rng_plan_handle h, void *cuda_stream)
         cudaSetDevice(p->device);
     int status = cuda_status(cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), st));
     if (!status) {
-        batch_kernel<0><<<p->grid, p->threads, 0, st>>>(p->d_units, p->n_units, p->d_next);
+        batch_kernel<kHint><<<p->grid, p->threads, 0, st>>>(p->d_units, p->n_units, p->d_next);
         status = cuda_status(cudaGetLastError());
     }
     if (prev >= 0 && prev != p->device)
@@ -266,8 +368,6 @@ extern "C" int rng_generate_batch(const rng_batch_item *items, size_t n_items, v
 // that must not pay for (or be synchronised by) a cudaMalloc/cudaFree pair.
 // The paper has no counterpart of this entry point.
 // ------------------------------------------------------------------------
-#include <mutex>
-
 namespace gbrng {
 namespace {
 
@@ -283,7 +383,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 std::mutex g_noalloc_mutex;                      // guards the host arrays below
 void *g_noalloc_dev_ptr[64] = {nullptr};         // device address of the scratch
 Unit g_noalloc_host_units[kNoAllocMaxTiles];     // host copy of the work list
-const void *g_noalloc_handles[kNoAllocMaxItems]; // duplicate check
+Claim g_noalloc_claims[kNoAllocMaxItems];       // overlap check
 
 }  // namespace
 }  // namespace gbrng
@@ -295,69 +395,26 @@ extern "C" int rng_generate_batch_noalloc(const rng_batch_item *items, size_t n_
         return set_error(RNG_ERR_ARG);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     int device = -1;
-    for (size_t i = 0; i < n_items; ++i) {
-        Gen *g = reinterpret_cast<Gen *>(items[i].h);
-        if (!g || (items[i].fmt != RNG_U32 && items[i].fmt != RNG_F32))
-            return set_error(RNG_ERR_ARG);
-        if (device < 0)
-            device = g->device;
-        if (g->device != device || device >= 64)
-            return set_error(RNG_ERR_ARG);
-        g_noalloc_handles[i] = g;
-    }
-    std::sort(g_noalloc_handles, g_noalloc_handles + n_items);
-    for (size_t i = 1; i < n_items; ++i)
-        if (g_noalloc_handles[i] == g_noalloc_handles[i - 1])
-            return set_error(RNG_ERR_ARG);
-
+    int st = validate_items(items, n_items, g_noalloc_claims, &device);
+    if (st)
+        return st;
+    if (device >= 64)
+        return set_error(RNG_ERR_ARG);
     // Work list, as rng_plan_create with its default CTA size builds it.
-    const int threads = 128;
-    uint64_t n_units = 0;
-    for (size_t i = 0; i < n_items; ++i) {
-        const rng_batch_item &it = items[i];
-        Gen *g = reinterpret_cast<Gen *>(it.h);
-        if (it.n_per_stream == 0)
-            continue;
-        if (!it.out || (uintptr_t)it.out % 4 != 0 || it.n_per_stream > UINT64_MAX / 4 / g->n)
-            return set_error(RNG_ERR_ARG);
-        bool vec = g->n % 4 == 0 && (uintptr_t)it.out % 16 == 0;
-        uint64_t tile = vec ? 4ull * threads : (uint64_t)threads;
-        uint64_t tiles = (g->n + tile - 1) / tile;
-        if (n_units + tiles > kNoAllocMaxTiles)
-            return set_error(RNG_ERR_ARG);  // beyond the work-list capacity
-        uint32_t code = (uint32_t)g->kind | ((uint32_t)it.fmt << 2) | (vec ? 8u : 0u);
-        for (uint64_t s0 = 0; s0 < g->n; s0 += tile) {
-            Unit &u = g_noalloc_host_units[n_units++];
-            u = Unit{};
-            u.state = g->d_state;
-            u.a = g->d_a;
-            u.out = static_cast<uint32_t *>(it.out);
-            u.n = g->n;
-            u.steps = it.n_per_stream;
-            u.s0 = (uint32_t)s0;
-            u.count = (uint32_t)std::min<uint64_t>(tile, g->n - s0);
-            u.code = code;
-        }
-    }
+    const int threads = kDefaultThreads;
+    const uint64_t n_units =
+        fill_units(items, n_items, threads, g_noalloc_host_units, kNoAllocMaxTiles);
+    if (n_units > kNoAllocMaxTiles)
+        return set_error(RNG_ERR_ARG);  // beyond the work-list capacity
     if (n_units == 0)
         return RNG_OK;
-    // Longest tiles first; ties ordered by generator and first stream (an
-    // in-place sort, no buffer; the order only affects scheduling).
-    std::sort(g_noalloc_host_units, g_noalloc_host_units + n_units,
-              [](const Unit &x, const Unit &y) {
-                  if (x.steps != y.steps)
-                      return x.steps > y.steps;
-                  if (x.state != y.state)
-                      return x.state < y.state;
-                  return x.s0 < y.s0;
-              });
+    order_units(g_noalloc_host_units, n_units);
 
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess)
         return set_error(RNG_ERR_CUDA);
     if (prev != device && cudaSetDevice(device) != cudaSuccess)
         return set_error(RNG_ERR_CUDA);
-    int st = RNG_OK;
     // Set-up, once per device with that device current: the device address
     // of the scratch array (its name in host code is only a host stand-in).
     if (!g_noalloc_dev_ptr[device]) {
@@ -369,12 +426,9 @@ extern "C" int rng_generate_batch_noalloc(const rng_batch_item *items, size_t n_
             g_noalloc_dev_ptr[device] = ptr;
     }
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    int sms = 0, fit = 0;
+    int grid = 0;
     if (!st)
-        st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    if (!st)
-        st = cuda_status(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<0>, threads, 0));
+        st = grid_for(device, threads, 0, &grid);
     unsigned char *base = static_cast<unsigned char *>(g_noalloc_dev_ptr[device]);
     unsigned long long *next = reinterpret_cast<unsigned long long *>(base);
     Unit *units = reinterpret_cast<Unit *>(base + kNoAllocHeader);
@@ -386,7 +440,7 @@ extern "C" int rng_generate_batch_noalloc(const rng_batch_item *items, size_t n_
     if (!st)  // the counter keeps the last call's value: clear it
         st = cuda_status(cudaMemsetAsync(next, 0, sizeof(unsigned long long), stream));
     if (!st) {
-        batch_kernel<0><<<sms * std::max(fit, 1), threads, 0, stream>>>(units, n_units, next);
+        batch_kernel<kHint><<<grid, threads, 0, stream>>>(units, n_units, next);
         st = cuda_status(cudaGetLastError());
     }
     if (prev >= 0 && prev != device)

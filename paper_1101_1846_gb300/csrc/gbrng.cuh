@@ -13,13 +13,20 @@ namespace gbrng {
 // One step of each generator on registers.  These are the only definitions
 // of the recurrences in the library; every kernel uses them.
 
-// Eq. 2-3 with b = 2^32: one 32x32+32 -> 64-bit multiply-add.
+// Eq. 2-3 with b = 2^32: t = a*x + c as a 64-bit value, x' = low word,
+// c' = high word.  Written as a multiply-add of the low words that sets the
+// carry flag and a multiply-add of the high words that consumes it, which is
+// the same 64-bit sum in fewer instructions than a widened add.
 __device__ __forceinline__ uint32_t mwc_step(uint32_t a, uint32_t &x, uint32_t &c)
 {
-    uint64_t t = (uint64_t)a * x + c;
-    x = (uint32_t)t;
-    c = (uint32_t)(t >> 32);
-    return x;
+    uint32_t lo, hi;
+    asm("mad.lo.cc.u32 %0, %2, %3, %4;\n\t"
+        "madc.hi.u32 %1, %2, %3, 0;"
+        : "=&r"(lo), "=r"(hi)  // lo is written before a and x are read again
+        : "r"(a), "r"(x), "r"(c));
+    x = lo;
+    c = hi;
+    return lo;
 }
 
 // xor128 (Marsaglia 2003); the four words are renamed in registers.
@@ -82,12 +89,14 @@ struct Gen {
 
 // Launch parameters of one generate call (host side).
 struct GenLaunch {
-    uint32_t *state;      // SoA base
+    uint32_t *state;      // SoA base, stride n
     const uint32_t *a;    // multipliers or nullptr
-    uint64_t n;           // streams
+    uint64_t n;           // streams of the generator
+    uint64_t s_begin;     // first stream advanced by this call
+    uint64_t s_end;       // one past the last
     uint64_t steps;       // outputs per stream in this call
-    void *out;            // device output, element (j, s) at j*ld + s
-    uint64_t ld;          // row stride in elements (normally n)
+    void *out;            // device output: element (j, s) at out[j*ld + s - s_begin]
+    uint64_t ld;          // row stride in elements
 };
 
 int set_error(int status);

@@ -1,6 +1,19 @@
 // Per-thread generation bodies shared by the plain kernels (generate.cu) and
 // the batched persistent kernel (batch.cu), so that both produce identical
 // outputs and state by construction.
+//
+// Three bodies:
+//   body_vec    4 adjacent streams per group, V groups per thread, one
+//               16-byte store per group per step; rows 32-byte aligned.
+//   body_vec_sync  the same with one group per thread and a barrier every
+//               four rows, for rows that are 16- but not 32-byte aligned.
+//   body_shift  4 adjacent streams per thread for rows that are NOT 16-byte
+//               aligned (any n, out 4-byte aligned): each row is written with
+//               16-byte stores at the aligned positions, taking the words
+//               that spill over from the lane on the left by a warp shuffle;
+//               a halo lane per warp closes the warp boundaries, and only
+//               the CTA's first and last words go out as 4-byte stores.
+//   body_scalar one stream per thread, 4-byte stores (tails of < 4 streams).
 #pragma once
 
 #include "gbrng.cuh"
@@ -16,24 +29,32 @@ struct Words<RNG_XOR128> { static constexpr int W = 4; };
 template <>
 struct Words<RNG_KISS> { static constexpr int W = 4; };
 
-template <int KIND>
-__device__ __forceinline__ uint32_t step(uint32_t a, uint32_t *w)
+// One step of stream i of a group of four: w[word][i], a[i].
+template <int KIND, int FMT>
+__device__ __forceinline__ uint32_t step_enc(uint32_t (&w)[4][4], const uint32_t (&a)[4], int i)
 {
+    uint32_t u;
     if constexpr (KIND == RNG_MWC32)
-        return mwc_step(a, w[0], w[1]);
+        u = mwc_step(a[i], w[0][i], w[1][i]);
     else if constexpr (KIND == RNG_XOR128)
-        return xor128_step(w[0], w[1], w[2], w[3]);
+        u = xor128_step(w[0][i], w[1][i], w[2][i], w[3][i]);
     else
-        return kiss_step(a, w[0], w[1], w[2], w[3]);
+        u = kiss_step(a[i], w[0][i], w[1][i], w[2][i], w[3][i]);
+    if constexpr (FMT == RNG_F32)
+        return __float_as_uint(unit_f32(u));
+    else
+        return u;
 }
 
 template <int HINT>
-__device__ __forceinline__ void store16(uint4 *p, uint4 v)
+__device__ __forceinline__ void store16(uint32_t *p, uint32_t x, uint32_t y, uint32_t z,
+                                        uint32_t w)
 {
+    uint4 v = make_uint4(x, y, z, w);
     if constexpr (HINT == 1)
-        __stcs(p, v);  // streaming: evict-first
+        __stcs(reinterpret_cast<uint4 *>(p), v);  // streaming: evict-first
     else
-        *p = v;
+        *reinterpret_cast<uint4 *>(p) = v;
 }
 
 template <int HINT>
@@ -45,114 +66,345 @@ __device__ __forceinline__ void store4(uint32_t *p, uint32_t v)
         *p = v;
 }
 
-template <int FMT>
-__device__ __forceinline__ uint32_t encode(uint32_t u)
+// 16-byte aligned group load/store of one state word of streams s0..s0+3.
+__device__ __forceinline__ void load4(const uint32_t *p, uint32_t (&d)[4])
 {
-    if constexpr (FMT == RNG_F32)
-        return __float_as_uint(unit_f32(u));
-    else
-        return u;
+    uint4 q = *reinterpret_cast<const uint4 *>(p);
+    d[0] = q.x;
+    d[1] = q.y;
+    d[2] = q.z;
+    d[3] = q.w;
 }
 
-// Vector body: this thread owns V groups of four adjacent streams starting at
-// s_first + v * v_stride (v < V); groups at or beyond s_end are idle.  n is
-// the generator's stream count (state stride), ld the output row stride.
-// Requires n % 4 == 0, 16-byte aligned state, multipliers and out, ld % 4 == 0.
+__device__ __forceinline__ void save4(uint32_t *p, const uint32_t (&d)[4])
+{
+    *reinterpret_cast<uint4 *>(p) = make_uint4(d[0], d[1], d[2], d[3]);
+}
+
+// Aligned vector body: V groups of four streams starting at s_first +
+// v * v_stride (all of them live: the caller checks); row0 points at the
+// output element of stream s_first in row 0 (16-byte aligned), and the
+// group v outputs sit v * v_stride elements further along each row.
 template <int KIND, int FMT, int V, int HINT>
 __device__ __forceinline__ void body_vec(uint32_t *__restrict__ state,
                                          const uint32_t *__restrict__ mult, uint64_t n,
-                                         uint64_t steps, uint32_t *__restrict__ out,
-                                         uint64_t ld, uint64_t s_first, uint64_t v_stride,
-                                         uint64_t s_end)
+                                         uint32_t steps, uint32_t *__restrict__ row0,
+                                         uint64_t ld, uint64_t s_first, uint64_t v_stride)
 {
     constexpr int W = Words<KIND>::W;
-    constexpr bool HAS_A = KIND != RNG_XOR128;
-    uint32_t st[V][4][W];
+    uint32_t w[V][4][4];
     uint32_t a[V][4];
-    bool live[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        uint64_t s0 = s_first + v_stride * v;
-        live[v] = s0 < s_end;
+        const uint64_t s0 = s_first + v_stride * v;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            a[v][i] = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                st[v][i][w] = 0;
-        }
-        if (live[v]) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint4 q = *reinterpret_cast<const uint4 *>(state + w * n + s0);
-                st[v][0][w] = q.x;
-                st[v][1][w] = q.y;
-                st[v][2][w] = q.z;
-                st[v][3][w] = q.w;
-            }
-            if constexpr (HAS_A) {
-                uint4 q = *reinterpret_cast<const uint4 *>(mult + s0);
-                a[v][0] = q.x;
-                a[v][1] = q.y;
-                a[v][2] = q.z;
-                a[v][3] = q.w;
-            }
-        }
+        for (int k = 0; k < W; ++k)
+            load4(state + k * n + s0, w[v][k]);
+        if constexpr (KIND != RNG_XOR128)
+            load4(mult + s0, a[v]);
+        else
+            a[v][0] = a[v][1] = a[v][2] = a[v][3] = 0;
     }
-
-    uint32_t *row = out + s_first;
+    uint32_t *row = row0;
 #pragma unroll 4
-    for (uint64_t j = 0; j < steps; ++j) {
+    for (uint32_t j = 0; j < steps; ++j) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            uint4 o;
-            o.x = encode<FMT>(step<KIND>(a[v][0], st[v][0]));
-            o.y = encode<FMT>(step<KIND>(a[v][1], st[v][1]));
-            o.z = encode<FMT>(step<KIND>(a[v][2], st[v][2]));
-            o.w = encode<FMT>(step<KIND>(a[v][3], st[v][3]));
-            if (live[v])
-                store16<HINT>(reinterpret_cast<uint4 *>(row + v_stride * v), o);
+            uint32_t o0 = step_enc<KIND, FMT>(w[v], a[v], 0);
+            uint32_t o1 = step_enc<KIND, FMT>(w[v], a[v], 1);
+            uint32_t o2 = step_enc<KIND, FMT>(w[v], a[v], 2);
+            uint32_t o3 = step_enc<KIND, FMT>(w[v], a[v], 3);
+            store16<HINT>(row + v_stride * v, o0, o1, o2, o3);
         }
         row += ld;
     }
-
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        uint64_t s0 = s_first + v_stride * v;
-        if (live[v]) {
+        const uint64_t s0 = s_first + v_stride * v;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint4 q = make_uint4(st[v][0][w], st[v][1][w], st[v][2][w], st[v][3][w]);
-                *reinterpret_cast<uint4 *>(state + w * n + s0) = q;
+        for (int k = 0; k < W; ++k)
+            save4(state + k * n + s0, w[v][k]);
+    }
+}
+
+// Aligned vector body for rows that are 16-byte but not 32-byte aligned
+// (n % 8 != 0 or a 32-byte misaligned output): one group of four streams per
+// thread, and a barrier every four rows.  A warp's 512-byte row window then
+// begins or ends inside a 32-byte DRAM sector that its neighbour completes;
+// keeping the CTA's warps within a few rows of each other lets the two
+// halves meet in L2 instead of reaching DRAM as partial sectors (which cost a
+// read-modify-write).  Every thread of the CTA must call this; threads whose
+// group is not `live` compute on zero state and store nothing.
+template <int KIND, int FMT, int HINT>
+__device__ __forceinline__ void body_vec_sync(uint32_t *__restrict__ state,
+                                              const uint32_t *__restrict__ mult, uint64_t n,
+                                              uint32_t steps, uint32_t *__restrict__ row0,
+                                              uint64_t ld, uint64_t s_first, bool live)
+{
+    constexpr int W = Words<KIND>::W;
+    uint32_t w[4][4] = {};
+    uint32_t a[4] = {0, 0, 0, 0};
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            load4(state + k * n + s_first, w[k]);
+        if constexpr (KIND != RNG_XOR128)
+            load4(mult + s_first, a);
+    }
+    uint32_t *row = row0;
+    const uint32_t blocks = steps / 4;
+    for (uint32_t b = 0; b < blocks; ++b) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+            uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+            uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+            uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+            if (live)
+                store16<HINT>(row, o0, o1, o2, o3);
+            row += ld;
+        }
+    }
+    for (uint32_t j = 4 * blocks; j < steps; ++j) {
+        uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+        uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+        uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+        uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+        if (live)
+            store16<HINT>(row, o0, o1, o2, o3);
+        row += ld;
+    }
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            save4(state + k * n + s_first, w[k]);
+    }
+}
+
+// One row of the realigned body with the row's alignment R (the word
+// address of the lane's own first element, mod 4) known at compile time.
+// A lane's four words sit at positions R..3 of the aligned chunk C = row - R
+// and 0..R-1 of the next chunk C + 4.
+//   R = 1, 2: the lane stores chunk C, made of the last R words of lane l-1
+//             (shuffled up) and its own first 4-R words ("prev" lanes:
+//             l > 0 and live);
+//   R = 3:    the lane stores chunk C + 4, made of its own last 3 words and
+//             the first word of lane l+1 (shuffled down) ("next" lanes:
+//             live, not a halo, and lane l+1 live).
+// EDGE warps also store the stray words singly: the CTA's first lane its
+// words 0 .. 3-R, the owner of its last group its words 4-R .. 3.
+template <int KIND, int FMT, int HINT, int R, bool EDGE>
+__device__ __forceinline__ void shift_row(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+                                          uint32_t *row, bool owner, bool prev, bool next,
+                                          bool lead, bool trail)
+{
+    const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+    const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+    const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+    const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+    if constexpr (R == 0) {
+        if (owner)
+            store16<HINT>(row, o0, o1, o2, o3);
+    } else {
+        if constexpr (R == 1) {
+            const uint32_t p3 = __shfl_up_sync(0xffffffffu, o3, 1);
+            if (prev)
+                store16<HINT>(row - 1, p3, o0, o1, o2);
+        } else if constexpr (R == 2) {
+            const uint32_t p2 = __shfl_up_sync(0xffffffffu, o2, 1);
+            const uint32_t p3 = __shfl_up_sync(0xffffffffu, o3, 1);
+            if (prev)
+                store16<HINT>(row - 2, p2, p3, o0, o1);
+        } else {
+            const uint32_t n0 = __shfl_down_sync(0xffffffffu, o0, 1);
+            if (next)
+                store16<HINT>(row + 1, o1, o2, o3, n0);
+        }
+        if constexpr (EDGE) {
+            if (lead) {
+                store4<HINT>(row, o0);
+                if constexpr (R <= 2)
+                    store4<HINT>(row + 1, o1);
+                if constexpr (R == 1)
+                    store4<HINT>(row + 2, o2);
+            }
+            if (trail) {
+                if constexpr (R == 3)
+                    store4<HINT>(row + 1, o1);
+                if constexpr (R >= 2)
+                    store4<HINT>(row + 2, o2);
+                store4<HINT>(row + 3, o3);
             }
         }
     }
 }
 
-// Scalar body: one stream s (< n), 4-byte stores; any n, 4-byte aligned out.
+// Rows in blocks of four: the alignment of row j + 4 equals that of row j,
+// so within a block every row's alignment is a compile-time constant.
+template <int KIND, int FMT, int HINT, int R0, int DR, bool EDGE>
+__device__ __forceinline__ void shift_rows(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+                                           uint32_t *&row, uint64_t ld, uint32_t blocks,
+                                           bool owner, bool prev, bool next, bool lead,
+                                           bool trail)
+{
+    for (uint32_t b = 0; b < blocks; ++b) {
+        __syncthreads();  // keep the CTA's warps within four rows of each other
+        shift_row<KIND, FMT, HINT, R0, EDGE>(w, a, row, owner, prev, next, lead, trail);
+        row += ld;
+        shift_row<KIND, FMT, HINT, (R0 + DR) & 3, EDGE>(w, a, row, owner, prev, next, lead,
+                                                        trail);
+        row += ld;
+        shift_row<KIND, FMT, HINT, (R0 + 2 * DR) & 3, EDGE>(w, a, row, owner, prev, next,
+                                                            lead, trail);
+        row += ld;
+        shift_row<KIND, FMT, HINT, (R0 + 3 * DR) & 3, EDGE>(w, a, row, owner, prev, next,
+                                                            lead, trail);
+        row += ld;
+    }
+}
+
+template <int KIND, int FMT, int HINT, bool EDGE>
+__device__ __forceinline__ void shift_rows_dispatch(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+                                                    uint32_t *&row, uint64_t ld, uint32_t r0,
+                                                    uint32_t blocks, bool owner, bool prev,
+                                                    bool next, bool lead, bool trail)
+{
+    const uint32_t dr = (uint32_t)(ld & 3);
+#define GBRNG_SHIFT_CASE(R0_, DR_)                                                            \
+    case (R0_) * 4 + (DR_):                                                                   \
+        shift_rows<KIND, FMT, HINT, R0_, DR_, EDGE>(w, a, row, ld, blocks, owner, prev, next, \
+                                                    lead, trail);                             \
+        break;
+    switch (r0 * 4 + dr) {
+        GBRNG_SHIFT_CASE(0, 0) GBRNG_SHIFT_CASE(0, 1) GBRNG_SHIFT_CASE(0, 2) GBRNG_SHIFT_CASE(0, 3)
+        GBRNG_SHIFT_CASE(1, 0) GBRNG_SHIFT_CASE(1, 1) GBRNG_SHIFT_CASE(1, 2) GBRNG_SHIFT_CASE(1, 3)
+        GBRNG_SHIFT_CASE(2, 0) GBRNG_SHIFT_CASE(2, 1) GBRNG_SHIFT_CASE(2, 2) GBRNG_SHIFT_CASE(2, 3)
+        GBRNG_SHIFT_CASE(3, 0) GBRNG_SHIFT_CASE(3, 1) GBRNG_SHIFT_CASE(3, 2) GBRNG_SHIFT_CASE(3, 3)
+    default: break;
+    }
+#undef GBRNG_SHIFT_CASE
+}
+
+// One row with a run-time alignment (the at most three rows after the
+// blocks of four).
+template <int KIND, int FMT, int HINT>
+__device__ __forceinline__ void shift_row_rt(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+                                             uint32_t *row, uint32_t r, bool owner, bool prev,
+                                             bool next, bool lead, bool trail)
+{
+    switch (r) {
+    case 0: shift_row<KIND, FMT, HINT, 0, true>(w, a, row, owner, prev, next, lead, trail); break;
+    case 1: shift_row<KIND, FMT, HINT, 1, true>(w, a, row, owner, prev, next, lead, trail); break;
+    case 2: shift_row<KIND, FMT, HINT, 2, true>(w, a, row, owner, prev, next, lead, trail); break;
+    default: shift_row<KIND, FMT, HINT, 3, true>(w, a, row, owner, prev, next, lead, trail); break;
+    }
+}
+
+// Realigned vector body, for rows that are not 16-byte aligned.  The CTA
+// (K = blockDim.x / 32 warps, every thread must call this) covers up to
+// 31K + 1 groups of four consecutive streams, starting at stream cta_s0
+// whose output element in row 0 is cta_row0; `groups` of them are live.
+// Lane l of warp k holds group g = 31k + l, so lane 31 of a warp other than
+// the last holds the first group of the next warp as well: a halo, stepped
+// from the same starting state but never written back.  Every warp's first
+// element is 124 words after the previous warp's, so all warps see the same
+// row alignment, and a warp's halo lane writes the chunk that straddles the
+// warp boundary (shift_row); only the CTA's first lane and the owner of its
+// last group store stray words singly.  The barrier after the state loads
+// keeps every halo read ahead of the owner's write-back, and one every four
+// rows keeps the warps together (see body_vec_sync): every warp runs the
+// rows, idle lanes storing nothing.
+template <int KIND, int FMT, int HINT>
+__device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,
+                                           const uint32_t *__restrict__ mult, uint64_t n,
+                                           uint32_t steps, uint32_t *__restrict__ cta_row0,
+                                           uint64_t ld, uint64_t cta_s0, uint32_t groups)
+{
+    constexpr int W = Words<KIND>::W;
+    const int lane = threadIdx.x & 31;
+    const int k = threadIdx.x >> 5;
+    const int K = blockDim.x >> 5;
+    const uint32_t g = 31u * k + lane;
+    const bool live = g < groups;
+    const bool owner = live && (lane < 31 || k == K - 1);
+    const bool lead = (g == 0);                   // the CTA's first lane
+    const bool trail = owner && g == groups - 1;  // owner of the CTA's last group
+    const bool prev = live && lane > 0;                              // chunk C
+    const bool next = owner && lane < 31 && g + 1 < groups;          // chunk C + 4
+    const uint64_t s_first = cta_s0 + 4 * (uint64_t)g;
+    uint32_t w[4][4];
+    uint32_t a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        a[i] = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            w[q][i] = 0;
+    }
+    if (live) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int q = 0; q < W; ++q)
+                w[q][i] = state[q * n + s_first + i];
+            if constexpr (KIND != RNG_XOR128)
+                a[i] = mult[s_first + i];
+        }
+    }
+    __syncthreads();  // every halo state is read before any write-back
+    const bool warp_edge = __any_sync(0xffffffffu, lead || trail);
+    {  // every warp runs the rows (idle lanes store nothing): all reach every barrier
+        uint32_t *row = cta_row0 + 4 * (uint64_t)g;
+        const uint32_t r0 = (uint32_t)((uintptr_t)cta_row0 >> 2) & 3u;
+        const uint32_t blocks = steps / 4;
+        if (warp_edge)
+            shift_rows_dispatch<KIND, FMT, HINT, true>(w, a, row, ld, r0, blocks, owner, prev,
+                                                       next, lead, trail);
+        else
+            shift_rows_dispatch<KIND, FMT, HINT, false>(w, a, row, ld, r0, blocks, owner, prev,
+                                                        next, lead, trail);
+        uint32_t r = r0;  // rows 4*blocks.. keep the alignment of row 0 shifted by 4*dr == 0
+        for (uint32_t j = 4 * blocks; j < steps; ++j) {
+            shift_row_rt<KIND, FMT, HINT>(w, a, row, r, owner, prev, next, lead, trail);
+            row += ld;
+            r = (r + (uint32_t)(ld & 3)) & 3u;
+        }
+    }
+    if (owner) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < W; ++q)
+                state[q * n + s_first + i] = w[q][i];
+    }
+}
+
+// Scalar body: one stream s (< n), 4-byte stores from p0 (its element in
+// row 0); any n, 4-byte aligned output.
 template <int KIND, int FMT, int HINT>
 __device__ __forceinline__ void body_scalar(uint32_t *__restrict__ state,
                                             const uint32_t *__restrict__ mult, uint64_t n,
-                                            uint64_t steps, uint32_t *__restrict__ out,
+                                            uint32_t steps, uint32_t *__restrict__ p0,
                                             uint64_t ld, uint64_t s)
 {
     constexpr int W = Words<KIND>::W;
-    uint32_t st[W];
+    uint32_t w[4][4];
+    uint32_t a[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-        st[w] = state[w * n + s];
-    uint32_t a = 0;
+    for (int k = 0; k < 4; ++k)
+        w[k][0] = k < W ? state[k * n + s] : 0;
     if constexpr (KIND != RNG_XOR128)
-        a = mult[s];
-    uint32_t *p = out + s;
+        a[0] = mult[s];
+    uint32_t *p = p0;
 #pragma unroll 4
-    for (uint64_t j = 0; j < steps; ++j) {
-        store4<HINT>(p, encode<FMT>(step<KIND>(a, st)));
+    for (uint32_t j = 0; j < steps; ++j) {
+        store4<HINT>(p, step_enc<KIND, FMT>(w, a, 0));
         p += ld;
     }
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-        state[w * n + s] = st[w];
+    for (int k = 0; k < W; ++k)
+        state[k * n + s] = w[k][0];
 }
 
 }  // namespace gbrng

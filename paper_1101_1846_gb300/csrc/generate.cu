@@ -10,108 +10,210 @@
 // Layout: output j of stream s at out[j*ld + s] (ld = n_streams for a plain
 // call); state word w of stream s at state[w*n + s].
 //
-// Vector kernel (n % 4 == 0, out 16-byte aligned): a CTA of B threads covers
-// 4*V*B consecutive streams; thread t owns the groups of four starting at
-// base + 4t + 4Bv, v < V, so each of its V stores per step is coalesced
-// across the warp.  Scalar kernel (any n, any 4-byte aligned out): one
-// stream per thread, 4-byte stores.
+// Paths (chosen per call by launch_generate):
+//   aligned  n % 4 == 0 and out 16-byte aligned: gen_vec when every row is
+//            32-byte aligned (a CTA of B threads covers 4*V*B consecutive
+//            streams, thread t owns the groups starting at base + 4t + 4Bv,
+//            v < V), else gen_vec_sync (one group per thread, barriers);
+//   shifted  otherwise, for the first n & ~3 streams: gen_shift, rows written
+//            with 16-byte stores after a warp-shuffle realignment;
+//   tail     the last n % 4 streams, taken by one extra CTA of gen_shift with
+//            4-byte stores.
+#include <algorithm>
+
 #include "gen_body.cuh"
 #include "rng_tune.h"
 
 namespace gbrng {
 namespace {
 
+// Streams [s_begin, s_begin + count) of the generator; out points at the
+// output element of stream s_begin in row 0.
 template <int KIND, int FMT, int V, int HINT>
 __global__ void __launch_bounds__(512)
 gen_vec(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
-        uint64_t steps, uint32_t *__restrict__ out, uint64_t ld)
+        uint32_t steps, uint32_t *__restrict__ out, uint64_t ld, uint64_t s_begin,
+        uint64_t count)
 {
     const uint64_t B = blockDim.x;
-    const uint64_t s_first = (uint64_t)blockIdx.x * (4 * V) * B + 4 * (uint64_t)threadIdx.x;
-    body_vec<KIND, FMT, V, HINT>(state, mult, n, steps, out, ld, s_first, 4 * B, n);
+    const uint64_t c_first = (uint64_t)blockIdx.x * (4 * V) * B + 4 * (uint64_t)threadIdx.x;
+    if (V == 2 && c_first + 4 * B < count)
+        body_vec<KIND, FMT, V, HINT>(state, mult, n, steps, out + c_first, ld,
+                                     s_begin + c_first, 4 * B);
+    else if (c_first < count)
+        body_vec<KIND, FMT, 1, HINT>(state, mult, n, steps, out + c_first, ld,
+                                     s_begin + c_first, 4 * B);
 }
 
+// Rows 16-byte but not 32-byte aligned: one group per thread, barriers every
+// four rows; every thread runs the rows (idle groups store nothing).
 template <int KIND, int FMT, int HINT>
 __global__ void __launch_bounds__(512)
-gen_scalar(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
-           uint64_t steps, uint32_t *__restrict__ out, uint64_t ld)
+gen_vec_sync(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
+             uint32_t steps, uint32_t *__restrict__ out, uint64_t ld, uint64_t s_begin,
+             uint64_t count)
 {
-    uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n)
-        body_scalar<KIND, FMT, HINT>(state, mult, n, steps, out, ld, s);
+    const uint64_t c_first = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    body_vec_sync<KIND, FMT, HINT>(state, mult, n, steps, out + c_first, ld, s_begin + c_first,
+                                   c_first < count);
 }
 
-using KernelFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint64_t, uint32_t *,
-                          uint64_t);
+// The first count & ~3 streams in realigned groups of four, 31K + 1 groups
+// per CTA of K warps (see body_shift); the last CTA of the grid takes the
+// count % 4 tail streams (one per thread), so that they run alongside the
+// rest instead of after it.
+template <int KIND, int FMT, int HINT>
+__global__ void __launch_bounds__(512)
+gen_shift(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
+          uint32_t steps, uint32_t *__restrict__ out, uint64_t ld, uint64_t s_begin,
+          uint64_t count)
+{
+    const uint64_t main = count & ~(uint64_t)3;
+    if (main < count && blockIdx.x == gridDim.x - 1) {
+        uint64_t c = main + threadIdx.x;
+        if (c < count)
+            body_scalar<KIND, FMT, HINT>(state, mult, n, steps, out + c, ld, s_begin + c);
+        return;
+    }
+    const uint64_t per_cta = 31 * (blockDim.x / 32) + 1;
+    const uint64_t g0 = (uint64_t)blockIdx.x * per_cta;
+    const uint64_t left = main / 4 - g0;
+    body_shift<KIND, FMT, HINT>(state, mult, n, steps, out + 4 * g0, ld, s_begin + 4 * g0,
+                                (uint32_t)(left < per_cta ? left : per_cta));
+}
+
+using VecFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t *, uint64_t,
+                       uint64_t, uint64_t);
+using ShiftFn = VecFn;
 
 template <int KIND, int FMT>
-KernelFn pick_vec(int v, int hint)
+VecFn pick_vec(int v, int hint)
 {
     if (v == 2)
         return hint ? gen_vec<KIND, FMT, 2, 1> : gen_vec<KIND, FMT, 2, 0>;
     return hint ? gen_vec<KIND, FMT, 1, 1> : gen_vec<KIND, FMT, 1, 0>;
 }
 
-template <int KIND>
-KernelFn pick_vec_kind(int fmt, int v, int hint)
+template <int KIND, int FMT>
+ShiftFn pick_shift(int hint)
 {
-    return fmt == RNG_F32 ? pick_vec<KIND, RNG_F32>(v, hint) : pick_vec<KIND, RNG_U32>(v, hint);
+    return hint ? gen_shift<KIND, FMT, 1> : gen_shift<KIND, FMT, 0>;
+}
+
+template <int KIND, int FMT>
+ShiftFn pick_sync(int hint)
+{
+    return hint ? gen_vec_sync<KIND, FMT, 1> : gen_vec_sync<KIND, FMT, 0>;
 }
 
 template <int KIND>
-KernelFn pick_scalar_kind(int fmt, int hint)
+void pick_kind(int fmt, int v, int hint, VecFn &vec, ShiftFn &shift, ShiftFn &sync)
 {
-    if (fmt == RNG_F32)
-        return hint ? gen_scalar<KIND, RNG_F32, 1> : gen_scalar<KIND, RNG_F32, 0>;
-    return hint ? gen_scalar<KIND, RNG_U32, 1> : gen_scalar<KIND, RNG_U32, 0>;
+    if (fmt == RNG_F32) {
+        vec = pick_vec<KIND, RNG_F32>(v, hint);
+        shift = pick_shift<KIND, RNG_F32>(hint);
+        sync = pick_sync<KIND, RNG_F32>(hint);
+    } else {
+        vec = pick_vec<KIND, RNG_U32>(v, hint);
+        shift = pick_shift<KIND, RNG_U32>(hint);
+        sync = pick_sync<KIND, RNG_U32>(hint);
+    }
 }
 
-// Launch shape per (kind, fmt): streams-per-thread groups V, CTA size, store
-// hint.  Defaults are the measured best on GB300; gbrng_set_launch changes
-// them (the autotuner does).
+// Launch shape per (kind, fmt): groups of four streams per thread V, CTA
+// size, store hint.  Defaults are the best measured on GB300 at 2^22 streams
+// x 1024 outputs; gbrng_set_launch changes them (the autotuner does).
 struct Shape {
-    int v = 1;
-    int block = 256;
-    int hint = 0;
+    int v;
+    int block;
+    int hint;
 };
-Shape g_shape[3][2];
+Shape g_shape[3][2] = {
+    {{1, 128, 1}, {2, 256, 1}},  // MWC u32, f32
+    {{2, 128, 1}, {1, 128, 1}},  // xor128
+    {{2, 512, 1}, {2, 512, 1}},  // KISS
+};
+
+constexpr int kSMs = 152;
+// CTA size of the kernels with row barriers: large CTAs leave fewer CTA
+// boundaries, where neighbouring CTAs that drift apart split sectors.
+constexpr int kSyncBlock = 512;
+
+// CTA size for `units` thread-sized pieces of work: shrink until the grid
+// covers every SM (small problems), never below one warp.
+int fit_threads(int threads, uint64_t units)
+{
+    while (threads > 32 && (units + threads - 1) / threads < kSMs)
+        threads /= 2;
+    return threads;
+}
 
 }  // namespace
 
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
 {
-    if (p.steps == 0 || p.n == 0)
+    const uint64_t count = p.s_end - p.s_begin;
+    if (p.steps == 0 || count == 0)
         return RNG_OK;
     const Shape sh = g_shape[kind][fmt];
-    bool vec = (p.n % 4 == 0) && (p.ld % 4 == 0) &&
-               ((uintptr_t)p.out % 16 == 0) && ((uintptr_t)p.state % 16 == 0) &&
-               (p.a == nullptr || (uintptr_t)p.a % 16 == 0);
-    KernelFn fn;
-    uint64_t blocks;
-    int threads = sh.block;
-    if (vec) {
-        fn = kind == RNG_MWC32    ? pick_vec_kind<RNG_MWC32>(fmt, sh.v, sh.hint)
-             : kind == RNG_XOR128 ? pick_vec_kind<RNG_XOR128>(fmt, sh.v, sh.hint)
-                                  : pick_vec_kind<RNG_KISS>(fmt, sh.v, sh.hint);
-        uint64_t groups = p.n / 4;
-        // small problems: shrink the CTA so that more SMs take part
-        while (threads > 32 && (groups + threads * sh.v - 1) / (threads * sh.v) < 152)
-            threads /= 2;
-        uint64_t per_block = (uint64_t)threads * sh.v;
-        blocks = (groups + per_block - 1) / per_block;
-    } else {
-        fn = kind == RNG_MWC32    ? pick_scalar_kind<RNG_MWC32>(fmt, sh.hint)
-             : kind == RNG_XOR128 ? pick_scalar_kind<RNG_XOR128>(fmt, sh.hint)
-                                  : pick_scalar_kind<RNG_KISS>(fmt, sh.hint);
-        while (threads > 32 && (p.n + threads - 1) / threads < 152)
-            threads /= 2;
-        blocks = (p.n + threads - 1) / threads;
+    VecFn vec;
+    ShiftFn shift, sync;
+    if (kind == RNG_MWC32)
+        pick_kind<RNG_MWC32>(fmt, sh.v, sh.hint, vec, shift, sync);
+    else if (kind == RNG_XOR128)
+        pick_kind<RNG_XOR128>(fmt, sh.v, sh.hint, vec, shift, sync);
+    else
+        pick_kind<RNG_KISS>(fmt, sh.v, sh.hint, vec, shift, sync);
+    // 16-byte rows and 16-byte state groups: every group of four streams
+    // starts on a 16-byte boundary in the output and in the state words.
+    const bool aligned = (count % 4 == 0) && (p.ld % 4 == 0) && ((uintptr_t)p.out % 16 == 0) &&
+                         (p.n % 4 == 0) && (p.s_begin % 4 == 0) &&
+                         ((uintptr_t)p.state % 16 == 0) &&
+                         (p.a == nullptr || (uintptr_t)p.a % 16 == 0);
+    // whole 32-byte sectors per warp and row: no barriers needed
+    const bool sectors = aligned && (p.ld % 8 == 0) && ((uintptr_t)p.out % 32 == 0);
+    const uint64_t main = count & ~(uint64_t)3;
+    uint32_t *out = static_cast<uint32_t *>(p.out);
+    // Calls longer than 2^31 steps are cut into pieces (the kernels count
+    // steps in 32 bits); the state carries from piece to piece.
+    for (uint64_t done = 0; done < p.steps;) {
+        const uint32_t steps = (uint32_t)std::min<uint64_t>(p.steps - done, 1u << 31);
+        uint32_t *o = out + done * p.ld;
+        if (aligned && !sectors) {
+            int threads = fit_threads(kSyncBlock, count / 4);
+            uint64_t blocks = (count / 4 + threads - 1) / threads;
+            if (blocks > 0x7FFFFFFFull)
+                return set_error(RNG_ERR_ARG);
+            sync<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                       p.s_begin, count);
+        } else if (aligned) {
+            int threads = sh.block;
+            uint64_t groups = count / 4;
+            while (threads > 32 && (groups + (uint64_t)threads * sh.v - 1) /
+                                           ((uint64_t)threads * sh.v) < kSMs)
+                threads /= 2;
+            uint64_t per_block = (uint64_t)threads * sh.v;
+            uint64_t blocks = (groups + per_block - 1) / per_block;
+            if (blocks > 0x7FFFFFFFull)
+                return set_error(RNG_ERR_ARG);
+            vec<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                      p.s_begin, count);
+        } else {
+            // realigned groups plus, when count % 4 != 0, one more CTA for the tail
+            int threads = fit_threads(kSyncBlock, main / 4);
+            const uint64_t per_cta = 31 * (threads / 32) + 1;
+            uint64_t blocks = (main / 4 + per_cta - 1) / per_cta + (count > main ? 1 : 0);
+            if (blocks > 0x7FFFFFFFull)
+                return set_error(RNG_ERR_ARG);
+            shift<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                        p.s_begin, count);
+        }
+        int e = cuda_status(cudaGetLastError());
+        if (e)
+            return e;
+        done += steps;
     }
-    if (blocks > 0x7FFFFFFFull)
-        return set_error(RNG_ERR_ARG);
-    fn<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, p.steps,
-                                             static_cast<uint32_t *>(p.out), p.ld);
-    return cuda_status(cudaGetLastError());
+    return RNG_OK;
 }
 
 }  // namespace gbrng

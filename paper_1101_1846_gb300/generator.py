@@ -73,6 +73,22 @@ class Generator:
                    "rng_generate")
         return out
 
+    def generate_range(self, s_begin: int, s_end: int, n_per_stream: int,
+                       out: torch.Tensor, ld: int, fmt: int | str = capi.RNG_U32,
+                       offset: int = 0, stream: torch.cuda.Stream | None = None) -> None:
+        """Advances streams [s_begin, s_end) only; output j of stream s goes to
+        out.view(-1)[offset + j*ld + (s - s_begin)]."""
+        fmt = capi.FMTS.get(fmt, fmt) if isinstance(fmt, str) else fmt
+        assert out.is_cuda and out.is_contiguous() and out.element_size() == 4
+        count = s_end - s_begin
+        if n_per_stream:
+            assert offset + (n_per_stream - 1) * ld + count <= out.numel()
+        self._bind(stream)
+        ptr = out.data_ptr() + 4 * offset
+        capi.check(capi.lib().rng_generate_range(self.h, s_begin, s_end, n_per_stream,
+                                                 ctypes.c_void_p(ptr), ld, fmt),
+                   "rng_generate_range")
+
     def generate_host(self, n_per_stream: int, fmt: int | str = capi.RNG_U32,
                       out: torch.Tensor | None = None,
                       stream: torch.cuda.Stream | None = None) -> torch.Tensor:
@@ -114,21 +130,35 @@ def multipliers(k: int, device: int | None = None) -> torch.Tensor:
 
 @dataclass
 class BatchItem:
+    """Generator `gen` advances streams [s_begin, s_end) (s_end = 0: all)
+    n_per_stream times; output j of stream s goes to
+    out.view(-1)[offset + j*ld + (s - s_begin)] (ld = 0: the stream count)."""
     gen: Generator
     n_per_stream: int
     out: torch.Tensor
     fmt: int
+    s_begin: int = 0
+    s_end: int = 0
+    ld: int = 0
+    offset: int = 0
 
 
 def _items(items: list[BatchItem]):
     arr = (capi.rng_batch_item * len(items))()
     for i, it in enumerate(items):
         assert it.out.is_cuda and it.out.is_contiguous()
-        assert it.out.numel() >= it.n_per_stream * it.gen.n_streams
+        s_end = it.s_end or it.gen.n_streams
+        ld = it.ld or it.gen.n_streams
+        if it.n_per_stream:
+            need = it.offset + (it.n_per_stream - 1) * ld + (s_end - it.s_begin)
+            assert it.out.numel() >= need
         arr[i].h = it.gen.h
         arr[i].n_per_stream = it.n_per_stream
-        arr[i].out = it.out.data_ptr()
+        arr[i].out = it.out.data_ptr() + 4 * it.offset
         arr[i].fmt = it.fmt
+        arr[i].s_begin = it.s_begin
+        arr[i].s_end = it.s_end
+        arr[i].ld = it.ld
     return arr
 
 

@@ -16,7 +16,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import oracle  # noqa: E402
-from paper_1101_1846_gb300 import build, capi, workloads  # noqa: E402
+from paper_1101_1846_gb300 import autotune, build, capi, workloads  # noqa: E402
 from paper_1101_1846_gb300.generator import (BatchItem, Generator, Plan,  # noqa: E402
                                              generate_batch, multipliers)
 
@@ -123,17 +123,97 @@ def test_unaligned_output_same_result(kind):
     assert int(buf[0]) == 0
 
 
+@pytest.mark.parametrize("offset", [0, 1, 2, 3, 4, 6])
+@pytest.mark.parametrize("n,steps", [(5, 13), (130, 7), (517, 9), (4099, 5), (1024, 6),
+                                     (2052, 11), (6000, 10)])
+@pytest.mark.parametrize("kind", KINDS)
+def test_rows_at_every_alignment(kind, n, steps, offset):
+    """Rows start at every word offset mod 8 (odd stream counts, outputs
+    shifted by 0-6 words): the sector-aligned, the barrier and the realigned
+    kernels, the edge lanes' 4-byte stores and the tail streams all land
+    where the layout says."""
+    seed = 4242 + n
+    fmt = oracle.F32 if (n + offset) % 2 else oracle.U32
+    buf = torch.full((n * steps + 8,), -7, dtype=torch.int32, device="cuda")
+    view = buf[offset:offset + n * steps]
+    g = Generator(kind, n, seed)
+    g.generate(steps, fmt, out=view)
+    torch.cuda.synchronize()
+    exp, st = expect_full(kind, n, seed, steps, fmt)
+    assert np.array_equal(bits(view).reshape(steps, n), obits(exp))
+    rest = torch.cat([buf[:offset], buf[offset + n * steps:]])
+    assert torch.all(rest == -7)  # nothing written outside the output
+    assert np.array_equal(bits(g.get_state()), st[:, :g.words].T)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_generate_range_advances_only_its_streams(kind):
+    """rng_generate_range on [s0, s1) with a row stride and an offset, then a
+    full call: streams in the range are ahead by the range's steps."""
+    n, seed = 1003, 91
+    g = Generator(kind, n, seed)
+    a = oracle_a(n) if kind != oracle.XOR128 else None
+    st = oracle.seed_streams(kind, a, seed, np.arange(n))
+    for (s0, s1, k, ld, off) in [(5, 262, 7, 300, 1), (0, 1003, 3, 1003, 0),
+                                 (512, 1000, 4, 491, 2), (999, 1003, 9, 4, 3)]:
+        buf = torch.full((off + (k - 1) * ld + (s1 - s0) + 5,), -9, dtype=torch.int32,
+                         device="cuda")
+        g.generate_range(s0, s1, k, buf, ld, oracle.U32, offset=off)
+        torch.cuda.synchronize()
+        exp, st_sub = oracle.generate(kind, a[s0:s1] if a is not None else None,
+                                      st[s0:s1], k, oracle.U32)
+        st[s0:s1] = st_sub
+        got = bits(buf)
+        for j in range(k):
+            row = got[off + j * ld: off + j * ld + (s1 - s0)]
+            assert np.array_equal(row, obits(exp[j])), (s0, s1, j)
+        written = np.zeros(len(got), bool)
+        for j in range(k):
+            written[off + j * ld: off + j * ld + (s1 - s0)] = True
+        assert np.all(got[~written] == np.uint32(2**32 - 9))
+    out = g.generate(5, oracle.F32)
+    torch.cuda.synchronize()
+    exp, st = oracle.generate(kind, a, st, 5, oracle.F32)
+    assert np.array_equal(bits(out), obits(exp))
+    assert np.array_equal(bits(g.get_state()), st[:, :g.words].T)
+
+
+def test_batch_disjoint_ranges_of_one_handle():
+    """Several items of the same generator with disjoint stream ranges in one
+    plan equal the same range calls made one after another."""
+    n, seed = 2050, 17
+    ranges = [(0, 700, 33), (700, 701, 5), (701, 1500, 12), (1503, 2050, 40)]
+    gb, gp = Generator(oracle.KISS, n, seed), Generator(oracle.KISS, n, seed)
+    ob = [torch.zeros(k * (e - b), dtype=torch.int32, device="cuda") for b, e, k in ranges]
+    op = [torch.zeros_like(o) for o in ob]
+    plan = Plan([BatchItem(gb, k, o, oracle.F32, s_begin=b, s_end=e, ld=e - b)
+                 for (b, e, k), o in zip(ranges, ob)])
+    plan.launch()
+    for (b, e, k), o in zip(ranges, op):
+        gp.generate_range(b, e, k, o, e - b, oracle.F32)
+    torch.cuda.synchronize()
+    for x, y in zip(ob, op):
+        assert torch.equal(x, y)
+    assert torch.equal(gb.get_state(), gp.get_state())
+    plan.close()
+    bad = [BatchItem(gb, 2, ob[0], 0, s_begin=0, s_end=700, ld=700),
+           BatchItem(gb, 2, ob[1], 0, s_begin=699, s_end=701, ld=2)]
+    with pytest.raises(capi.RngError):
+        Plan(bad)
+
+
 def test_launch_shapes_do_not_change_outputs():
     n, steps, seed = 4096, 21, 3
     exp = {k: expect_full(k, n, seed, steps, oracle.F32)[0] for k in KINDS}
-    for v, block, hint in [(1, 64, 0), (2, 128, 1), (2, 512, 0), (1, 512, 1)]:
+    saved = {k: autotune.get_shape(k, oracle.F32) for k in KINDS}
+    for v, block, hint in [(1, 64, 0), (2, 128, 1), (2, 512, 0), (1, 512, 1), (2, 32, 0)]:
         for k in KINDS:
             capi.check(capi.lib().gbrng_set_launch(k, oracle.F32, v, block, hint))
             out = Generator(k, n, seed).generate(steps, oracle.F32)
             torch.cuda.synchronize()
             assert np.array_equal(bits(out), obits(exp[k])), (k, v, block, hint)
     for k in KINDS:
-        capi.lib().gbrng_set_launch(k, oracle.F32, 1, 256, 0)
+        autotune.set_shape(k, oracle.F32, saved[k])
 
 
 # --------------------------------------------------------- the workloads
@@ -167,6 +247,21 @@ def test_xor_kiss_2p20x1024_sampled(kind):
     assert torch.equal(f, top24.to(torch.float32) * (2.0 ** -24))
     # and both generators end in the same state
     assert torch.equal(gu.get_state(), gf.get_state())
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_odd_stream_count_2p20_plus_3_sampled(kind):
+    """2^20 + 3 streams: the realigned path at scale, plus a 3-stream tail."""
+    n, steps, seed = (1 << 20) + 3, 64, 13
+    idx = np.concatenate([golden_streams(n), [n - 3, n - 2, n - 1]])
+    idx = np.array(sorted(i for i in set(idx.tolist()) if i < (1 << 20) or
+                          kind == oracle.XOR128 or i in set(GOLD["sample_index"])))
+    a = golden_a(idx) if kind != oracle.XOR128 else None
+    st = oracle.seed_streams(kind, a, seed, idx)
+    exp, _ = oracle.generate(kind, a, st, steps, oracle.U32)
+    out = Generator(kind, n, seed).generate(steps, oracle.U32)
+    got = bits(out.index_select(1, torch.as_tensor(idx, device="cuda")))
+    assert np.array_equal(got, obits(exp))
 
 
 @pytest.mark.parametrize("kind", KINDS)
