@@ -47,7 +47,14 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    p.add_argument("--workload", default="full", choices=["full", "batched"])
+    p.add_argument("--workload", default="full", choices=["full", "batched", "serving"])
+    p.add_argument("--rate", type=float, default=20_000.0, help="serving: arrivals/s")
+    p.add_argument("--duration", type=float, default=10.0, help="serving: seconds")
+    p.add_argument("--verify-every", type=int, default=100, help="serving: check every k-th")
+    p.add_argument("--serve-chunk-rows", type=int, default=1024,
+                   help="serving: most rows per client per tick")
+    p.add_argument("--tick-gib", type=float, default=8.0,
+                   help="serving: target output per tick, shared by busy clients")
     p.add_argument("--instances", type=int, default=10_000)
     p.add_argument("--wave-gib", type=float, default=24.0)
     p.add_argument("--tune", action="store_true", help="autotune launch shapes first")
@@ -518,12 +525,124 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------- serving
+def _probe_sequences(clients, streams, seed_of, rows, golden):
+    """Oracle outputs (uint32 and float32 bits) of a few streams per client,
+    rows 0 .. rows-1: the streams are golden-file indices, whose multipliers
+    the oracle wrote there."""
+    import numpy as np
+
+    import oracle
+    idx = [s for s in golden["sample_index"] if s < streams]
+    probes = [idx[0], idx[1], idx[255 % len(idx)], idx[-1]]
+    a_of = dict(zip(golden["sample_index"], golden["sample_a"]))
+    seqs = {}
+    for c in clients:
+        for s in probes:
+            a = np.array([a_of[s]], dtype=np.uint32)
+            st = oracle.seed_streams(2, a, seed_of(c), np.array([s]))[0]
+            u, _ = oracle.stream(2, int(a[0]), st, rows[c], 0)
+            f, _ = oracle.stream(2, int(a[0]), st, rows[c], 1)
+            seqs[(c, s)] = (u, f.view(np.uint32))
+    return probes, seqs
+
+
+def run_serving(args):
+    """Poisson arrivals at --rate requests/s for --duration s over 256
+    clients (65536-stream KISS generators resident on the device), sizes
+    log-uniform on [1 KiB, 256 MiB] (workloads.request_log), admission under
+    a 40 GB budget; real time, then the same requests all at once
+    (saturating).  Every --verify-every-th request is checked against the
+    oracle on four probe streams of its client."""
+    import numpy as np
+    import torch
+
+    from paper_1101_1846_gb300 import capi, workloads
+    from paper_1101_1846_gb300.serving import Server, replay
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    capi.lib()
+    n_clients, streams = 256, 65536
+    log = workloads.request_log(args.rate, args.duration, n_clients, 1024, 256 << 20, seed=5)
+    golden = json.loads((ROOT / "tests" / "golden" / "multipliers_b32.json").read_text())
+    chunk_rows = args.serve_chunk_rows
+    server = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
+                    budget_bytes=40 << 30, chunk_rows=chunk_rows,
+                    tick_bytes=int(args.tick_gib * (1 << 30)))
+    totals = {}
+    for r in log:
+        totals[r.client] = totals.get(r.client, 0) + r.n_samples
+    rows = {c: t // streams + 2 for c, t in totals.items()}
+    checked, bad = [0], [0]
+    probes, seqs = (None, None)
+    if args.verify_every > 0 and not args.no_verify:
+        probes, seqs = _probe_sequences(sorted(totals), streams, server.client_seed, rows,
+                                        golden)
+    active = []  # the engine being checked
+
+    def on_done(rid, req):
+        if probes is None or rid % args.verify_every:
+            return
+        srv = active[0]
+        info = srv.result(rid)
+        out = srv.copy(rid)
+        start, N = info["start"], info["n"]
+        for s in probes:
+            col = (s - start) % streams
+            if col >= N:
+                continue
+            cnt = (N - 1 - col) // streams + 1
+            pos = torch.arange(cnt, device="cuda", dtype=torch.int64) * streams + col
+            got = out[pos].cpu().numpy().view(np.uint32)
+            row0 = (start + col) // streams
+            u, f = seqs[(info["client"], s)]
+            exp = (u if info["fmt"] == 0 else f)[row0:row0 + cnt]
+            checked[0] += 1
+            if not np.array_equal(got, exp):
+                bad[0] += 1
+
+    live = replay(server, log, realtime=True).summary()
+    server.close()
+    # saturating run: the same requests, all submitted at once
+    server2 = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
+                     budget_bytes=40 << 30, chunk_rows=chunk_rows,
+                    tick_bytes=int(args.tick_gib * (1 << 30)))
+    sat = replay(server2, log, realtime=False).summary()
+    server2.close()
+    # untimed check: the same requests again, probing every k-th result
+    if probes is not None:
+        server3 = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
+                         budget_bytes=40 << 30, chunk_rows=chunk_rows,
+                    tick_bytes=int(args.tick_gib * (1 << 30)))
+        active.append(server3)
+        replay(server3, log, realtime=False, on_done=on_done)
+        server3.close()
+    line = {
+        "metric": METRIC, "workload": "serving", "impl": "ours",
+        "value": live["gsamples_s"], "unit": UNIT,
+        "p50_ms": live["p50_ms"], "p99_ms": live["p99_ms"], "mean_ms": live["mean_ms"],
+        "requests": live["requests"], "samples": live["samples"], "wall_s": live["wall_s"],
+        "offered_gsamples_s": sum(r.n_samples for r in log) / args.duration / 1e9,
+        "saturating": sat, "probe_checks": checked[0], "probe_mismatches": bad[0],
+        "bit_exact_probes": (bad[0] == 0) if checked[0] else None,
+        "max_arena_used_bytes": live["max_arena_used"], "ticks": live["ticks"],
+        "config": {"workload": "serving", "clients": n_clients, "streams_per_client": streams,
+                   "kind": "kiss", "rate_hz": args.rate, "duration_s": args.duration,
+                   "sizes": "log-uniform [1 KiB, 256 MiB]", "budget_bytes": 40 << 30,
+                   "chunk_rows": chunk_rows, "tick_bytes": int(args.tick_gib * (1 << 30)),
+                   "seed_base": args.seed},
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -212,6 +212,19 @@ rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n_items,
  * plan must not overlap on the device. */
 int rng_plan_launch(rng_plan_handle p, void *cuda_stream);
 
+/* Replaces the plan's work list with the tiles of a new set of items (same
+ * rules as rng_plan_create; the CTA size and grid stay), enqueueing the copy
+ * to the device on `cuda_stream`: a later rng_plan_launch on the same stream
+ * runs the new list, and a launch still in flight on that stream finishes
+ * with the old one.  The tiles keep the items' order (no length ordering),
+ * so that a serving loop can rebuild a plan every tick cheaply.  Allocates
+ * device memory only when the list outgrows every earlier one (after waiting
+ * for `cuda_stream`).  The host list is staged before the call returns.
+ * Errors: RNG_ERR_ARG (as rng_plan_create, or items on another device),
+ * RNG_ERR_OOM, RNG_ERR_CUDA. */
+int rng_plan_refill(rng_plan_handle p, const rng_batch_item *items, size_t n_items,
+                    void *cuda_stream);
+
 /* Tiles in the plan, and its CTA size and persistent grid size. */
 uint64_t rng_plan_tiles(rng_plan_handle p);
 int rng_plan_shape(rng_plan_handle p, int *threads, int *grid);
@@ -223,6 +236,106 @@ void rng_plan_destroy(rng_plan_handle p);
  * `cuda_stream`, wait for it, and free it.  SYNCHRONISES. */
 int rng_generate_batch(const rng_batch_item *items, size_t n_items,
                        void *cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Serving engine: many clients, each with its own device-resident
+ * generator of streams_per_client streams (seeded with seed_base + client
+ * id), answering requests for the next N samples of the client's sequence.
+ * Sample g of a client's sequence (g = 0, 1, ...) is output number
+ * g / streams_per_client of stream g % streams_per_client, so a client's
+ * sequence is the stream-interleaved output of its generator read row by
+ * row, and requests of one client take consecutive ranges of it in the
+ * order they were submitted.  Results are the same whatever other requests
+ * share the device (each is a function of its client and range only).
+ *
+ * The engine keeps submitted requests in a FIFO, admits a request when its
+ * output fits in the device arena (the HBM budget minus the generators'
+ * state), and on every tick runs one batched launch (a refilled plan) that
+ * advances every client with admitted work by one piece of at most
+ * chunk_rows rows of its current request: requests that arrive while others
+ * run join the next tick (continuous batching).  Up to two ticks are in
+ * flight on the engine's own CUDA stream.  A request's output (uint32 or
+ * float, N elements, contiguous, in sequence order) stays in the arena until
+ * it is released.  Not thread-safe: drive one engine from one host thread.
+ * Paper: none; the parametrised generators of Sec. "Parallelizing RNGs"
+ * served on demand.
+ * ------------------------------------------------------------------- */
+typedef struct rng_server *rng_server_handle;
+
+/* kind: any generator kind; n_clients >= 1; streams_per_client within the
+ * kind's maximum; budget_bytes: device memory for state plus outputs;
+ * chunk_rows >= 1.  Allocates everything up front (synchronises).  NULL on
+ * failure (rng_last_error(): RNG_ERR_ARG, RNG_ERR_OOM when the budget does
+ * not cover the state, RNG_ERR_CUDA, RNG_ERR_NODEV). */
+rng_server_handle rng_server_create(int kind, uint32_t n_clients,
+                                    uint64_t streams_per_client, uint64_t seed_base,
+                                    uint64_t budget_bytes, uint32_t chunk_rows);
+
+/* Queues a request for the next n_samples samples of `client` in format
+ * fmt; *req_id receives its id (ids count up from 0).  The request's range
+ * of the client's sequence is fixed here, at submission.  RNG_ERR_ARG for a
+ * bad client or fmt, n_samples = 0, or an output larger than the arena. */
+int rng_server_submit(rng_server_handle s, uint32_t client, uint64_t n_samples, int fmt,
+                      uint64_t *req_id);
+
+/* rng_server_submit for n requests at once (arrays of clients, sizes and
+ * formats; ids written to req_ids if not NULL), in array order.  Checks all
+ * of them first: nothing is queued if any is invalid. */
+int rng_server_submit_many(rng_server_handle s, const uint32_t *clients,
+                           const uint64_t *n_samples, const int *fmts, size_t n,
+                           uint64_t *req_ids);
+
+/* Does the engine's work without blocking: retires finished ticks, admits
+ * queued requests that now fit, and launches the next tick when fewer than
+ * two are in flight.  Returns the number of requests completed so far
+ * (ready to be taken), or a negative status. */
+int rng_server_progress(rng_server_handle s);
+
+/* Blocks until every submitted request has completed (driving progress). */
+int rng_server_drain(rng_server_handle s);
+
+/* Takes up to `cap` completed requests: ids[i] and done_ms[i], the device
+ * time of completion in milliseconds since the engine was created (from
+ * CUDA events).  Returns how many were taken. */
+int rng_server_take(rng_server_handle s, uint64_t *ids, double *done_ms, int cap);
+
+/* Where a completed (not yet released) request's output is: *dev_ptr (in
+ * the arena), *n_samples, *fmt, *client, *start (its first sample index in
+ * the client's sequence).  RNG_ERR_ARG for an unknown or released id. */
+int rng_server_result(rng_server_handle s, uint64_t req_id, void **dev_ptr,
+                      uint64_t *n_samples, int *fmt, uint32_t *client, uint64_t *start);
+
+/* Copies elements [offset, offset + count) of a completed request's output
+ * to dst (device or host memory) on cuda_stream (NULL: the engine's
+ * stream).  Asynchronous; release the request only after the copy is done. */
+int rng_server_copy(rng_server_handle s, uint64_t req_id, void *dst, uint64_t offset,
+                    uint64_t count, void *cuda_stream);
+
+/* Returns a completed request's output space to the arena. */
+int rng_server_release(rng_server_handle s, uint64_t req_id);
+
+/* rng_server_release for n requests; returns the first error, after
+ * releasing every valid id. */
+int rng_server_release_many(rng_server_handle s, const uint64_t *req_ids, size_t n);
+
+/* Counters: [0] submitted, [1] admitted, [2] completed, [3] ticks,
+ * [4] samples generated, [5] arena bytes in use, [6] arena bytes total,
+ * [7] requests waiting for admission. */
+int rng_server_stats(rng_server_handle s, uint64_t *out8);
+
+/* Sizes ticks by output bytes: each tick gives every client with admitted
+ * work an equal share of `bytes` (at least one row, at most chunk_rows
+ * rows), so that ticks stay short under light load (latency) and grow under
+ * a backlog (throughput).  0 (the default) gives every client chunk_rows
+ * rows per tick. */
+int rng_server_set_tick_bytes(rng_server_handle s, uint64_t bytes);
+
+/* The engine's CUDA stream (a cudaStream_t), e.g. to order a copy of a
+ * result after the tick that produced it. */
+void *rng_server_stream(rng_server_handle s);
+
+/* Waits for the engine's work and frees everything.  NULL is ignored. */
+void rng_server_destroy(rng_server_handle s);
 
 /* Allocation-free variant of rng_generate_batch, for callers that cannot
  * allocate device memory when they need samples: an application whose own

@@ -49,6 +49,8 @@ SIGNATURES = {
     "rng_plan_create": (ctypes.c_void_p, [ctypes.POINTER(rng_batch_item), ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int]),
     "rng_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "rng_plan_refill": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rng_batch_item),
+                                       ctypes.c_size_t, ctypes.c_void_p]),
     "rng_plan_tiles": (ctypes.c_uint64, [ctypes.c_void_p]),
     "rng_plan_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -57,6 +59,32 @@ SIGNATURES = {
                                           ctypes.c_void_p]),
     "rng_generate_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(rng_batch_item),
                                                   ctypes.c_size_t, ctypes.c_void_p]),
+    "rng_server_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]),
+    "rng_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    "rng_server_submit_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_void_p]),
+    "rng_server_progress": (ctypes.c_int, [ctypes.c_void_p]),
+    "rng_server_release_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_size_t]),
+    "rng_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
+    "rng_server_take": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "rng_server_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "rng_server_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
+    "rng_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rng_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "rng_server_set_tick_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rng_server_stream": (ctypes.c_void_p, [ctypes.c_void_p]),
+    "rng_server_destroy": (None, [ctypes.c_void_p]),
     "rng_last_error": (ctypes.c_int, []),
     "rng_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gbrng_set_launch": (ctypes.c_int, [ctypes.c_int] * 5),

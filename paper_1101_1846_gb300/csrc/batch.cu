@@ -219,9 +219,12 @@ struct Plan {
     int device = 0;
     Unit *d_units = nullptr;
     uint64_t n_units = 0;
+    uint64_t cap_units = 0;          // device work-list capacity
     unsigned long long *d_next = nullptr;
     int threads = kDefaultThreads;
     int grid = 0;
+    std::vector<Unit> host;          // refill staging
+    std::vector<Claim> claims;       // refill overlap check
 };
 
 void free_plan(Plan *p)
@@ -278,6 +281,7 @@ extern "C" rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n
             st = set_error(RNG_ERR_OOM);
         else
             st = cuda_status(cudaMemcpy(p->d_units, units.data(), bytes, cudaMemcpyHostToDevice));
+        p->cap_units = p->n_units;
     }
     if (!st && cudaMalloc(&p->d_next, sizeof(unsigned long long)) != cudaSuccess)
         st = set_error(RNG_ERR_OOM);
@@ -310,6 +314,49 @@ extern "C" int rng_plan_launch(rng_plan_handle h, void *cuda_stream)
     if (prev >= 0 && prev != p->device)
         cudaSetDevice(prev);
     return status;
+}
+
+extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, size_t n_items,
+                               void *cuda_stream)
+{
+    Plan *p = reinterpret_cast<Plan *>(h);
+    if (!p || !items || n_items == 0)
+        return set_error(RNG_ERR_ARG);
+    int device = -1;
+    p->claims.resize(n_items);
+    int st = validate_items(items, n_items, p->claims.data(), &device);
+    if (st)
+        return st;
+    if (device != p->device)
+        return set_error(RNG_ERR_ARG);
+    const uint64_t n = fill_units(items, n_items, p->threads, nullptr, 0);
+    p->host.resize(n);
+    fill_units(items, n_items, p->threads, p->host.data(), n);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device)
+        cudaSetDevice(p->device);
+    if (n > p->cap_units) {
+        // grow: wait for work that may still read the old list
+        st = cuda_status(cudaStreamSynchronize(stream));
+        Unit *grown = nullptr;
+        if (!st && cudaMalloc(&grown, n * sizeof(Unit)) != cudaSuccess)
+            st = set_error(RNG_ERR_OOM);
+        if (!st) {
+            cudaFree(p->d_units);
+            p->d_units = grown;
+            p->cap_units = n;
+        }
+    }
+    if (!st && n)  // pageable source: staged before the call returns
+        st = cuda_status(cudaMemcpyAsync(p->d_units, p->host.data(), n * sizeof(Unit),
+                                         cudaMemcpyHostToDevice, stream));
+    if (!st)
+        p->n_units = n;
+    if (prev >= 0 && prev != p->device)
+        cudaSetDevice(prev);
+    return st;
 }
 
 extern "C" uint64_t rng_plan_tiles(rng_plan_handle h)

@@ -1,0 +1,562 @@
+// Serving engine: device-resident client generators, an output arena under
+// an HBM budget, FIFO admission and continuous batching.  See the contract in
+// include/rng.h (rng_server_*).
+//
+// Sample g of a client's sequence is output g / n of stream g % n (n streams
+// per client).  A piece of m samples starting at sample c covers columns
+// 0 .. m-1 of a row-major window whose column `col` belongs to stream
+// (c % n + col) % n: columns below m % n get one output more than the others.
+// Each column range maps to at most two contiguous stream ranges (the window
+// wraps around stream n-1), so a piece is at most four batch items with
+// disjoint stream ranges of one generator, all in the same launch.
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "gbrng.cuh"
+
+namespace gbrng {
+namespace {
+
+constexpr uint64_t kGranule = 256;  // arena alignment, bytes
+constexpr int kMaxInflight = 2;
+constexpr int kServeThreads = 512;
+
+// First-fit allocator over [0, size) bytes in kGranule units.
+class Arena {
+public:
+    explicit Arena(uint64_t size) : size_(size / kGranule * kGranule)
+    {
+        if (size_)
+            free_[0] = size_;
+    }
+    bool alloc(uint64_t bytes, uint64_t *off)
+    {
+        bytes = (bytes + kGranule - 1) / kGranule * kGranule;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                uint64_t rest = it->second - bytes;
+                uint64_t at = it->first + bytes;
+                free_.erase(it);
+                if (rest)
+                    free_[at] = rest;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t bytes)
+    {
+        bytes = (bytes + kGranule - 1) / kGranule * kGranule;
+        used_ -= bytes;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + bytes == next->first) {
+            bytes += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    uint64_t used() const { return used_; }
+    uint64_t size() const { return size_; }
+
+private:
+    uint64_t size_;
+    uint64_t used_ = 0;
+    std::map<uint64_t, uint64_t> free_;
+};
+
+struct Req {
+    uint32_t client = 0;
+    uint64_t n = 0;      // samples
+    int fmt = 0;
+    uint64_t start = 0;  // first sample index in the client's sequence
+    uint64_t off = 0;    // arena byte offset
+    uint64_t done = 0;   // samples already scheduled
+    bool admitted = false;
+    bool completed = false;
+    double done_ms = 0;
+};
+
+struct Tick {
+    cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> completing;
+};
+
+struct Server {
+    int kind = 0;
+    int device = 0;
+    uint32_t n_clients = 0;
+    uint64_t streams = 0;
+    uint32_t chunk_rows = 0;
+    std::vector<rng_handle> gens;
+    uint32_t *arena_base = nullptr;
+    Arena *arena = nullptr;
+    std::vector<uint64_t> cursor;                 // next sample index per client
+    std::deque<uint64_t> pending;                 // waiting for admission
+    std::vector<std::deque<uint64_t>> active;     // admitted, per client, in order
+    std::unordered_map<uint64_t, Req> reqs;
+    std::deque<Tick> inflight;
+    std::vector<cudaEvent_t> spare_events;
+    std::deque<std::pair<uint64_t, double>> done;  // completed, not yet taken
+    std::vector<rng_batch_item> items;
+    rng_plan_handle plan = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t t0 = nullptr;
+    uint32_t rr = 0;  // round-robin start client
+    uint64_t tick_bytes = 0;  // target output per tick (0: chunk_rows alone)
+    uint64_t next_id = 0, n_admitted = 0, n_completed = 0, n_ticks = 0, samples = 0;
+};
+
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+// Items of one piece: m samples of `h` from sample c on, written to out.
+void piece_items(rng_handle h, uint64_t n, uint64_t c, uint64_t m, uint32_t *out, int fmt,
+                 std::vector<rng_batch_item> &items)
+{
+    const uint64_t r = c % n, q = m / n, rem = m % n;
+    auto columns = [&](uint64_t c0, uint64_t c1, uint64_t rows) {
+        if (rows == 0 || c0 >= c1)
+            return;
+        const uint64_t a1 = std::min(c1, n - r);  // columns [c0, a1): streams r + col
+        if (c0 < a1)
+            items.push_back(rng_batch_item{h, rows, out + c0, fmt, r + c0, r + a1, n});
+        const uint64_t b0 = std::max(c0, n - r);  // columns [b0, c1): streams col - (n - r)
+        if (b0 < c1)
+            items.push_back(
+                rng_batch_item{h, rows, out + b0, fmt, b0 - (n - r), c1 - (n - r), n});
+    };
+    columns(0, rem, q + 1);
+    columns(rem, n, q);
+}
+
+int retire(Server *S)
+{
+    while (!S->inflight.empty()) {
+        Tick &t = S->inflight.front();
+        cudaError_t e = cudaEventQuery(t.ev);
+        if (e == cudaErrorNotReady)
+            break;
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, S->t0, t.ev);
+        for (uint64_t id : t.completing) {
+            Req &q = S->reqs[id];
+            q.completed = true;
+            q.done_ms = ms;
+            S->done.emplace_back(id, (double)ms);
+            ++S->n_completed;
+        }
+        S->spare_events.push_back(t.ev);
+        S->inflight.pop_front();
+    }
+    return RNG_OK;
+}
+
+void admit(Server *S)
+{
+    while (!S->pending.empty()) {
+        Req &q = S->reqs[S->pending.front()];
+        uint64_t off = 0;
+        if (!S->arena->alloc(q.n * 4, &off))
+            break;  // first come, first served: later requests wait too
+        q.off = off;
+        q.admitted = true;
+        S->active[q.client].push_back(S->pending.front());
+        S->pending.pop_front();
+        ++S->n_admitted;
+    }
+}
+
+int launch_tick(Server *S)
+{
+    S->items.clear();
+    Tick tick;
+    uint64_t rows = S->chunk_rows;
+    if (S->tick_bytes) {
+        // an equal share of the target tick for every client with work
+        uint64_t busy = 0;
+        for (const auto &a : S->active)
+            busy += !a.empty();
+        const uint64_t share = busy ? S->tick_bytes / (busy * S->streams * 4) : rows;
+        rows = std::max<uint64_t>(1, std::min<uint64_t>(rows, share));
+    }
+    const uint64_t cap = rows * S->streams;
+    for (uint32_t k = 0; k < S->n_clients; ++k) {
+        const uint32_t c = (S->rr + k) % S->n_clients;
+        if (S->active[c].empty())
+            continue;
+        const uint64_t id = S->active[c].front();
+        Req &q = S->reqs[id];
+        const uint64_t m = std::min(q.n - q.done, cap);
+        uint32_t *out = S->arena_base + q.off / 4 + q.done;
+        piece_items(S->gens[c], S->streams, q.start + q.done, m, out, q.fmt, S->items);
+        q.done += m;
+        S->samples += m;
+        if (q.done == q.n) {
+            tick.completing.push_back(id);
+            S->active[c].pop_front();
+        }
+    }
+    S->rr = (S->rr + 1) % S->n_clients;
+    if (S->items.empty())
+        return RNG_OK;
+    int st;
+    if (!S->plan) {
+        S->plan = rng_plan_create(S->items.data(), S->items.size(), kServeThreads, 0);
+        st = S->plan ? RNG_OK : rng_last_error();
+    } else {
+        st = rng_plan_refill(S->plan, S->items.data(), S->items.size(), S->stream);
+    }
+    if (!st)
+        st = rng_plan_launch(S->plan, S->stream);
+    if (st)
+        return st;
+    if (S->spare_events.empty()) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess)
+            return set_error(RNG_ERR_CUDA);
+        S->spare_events.push_back(ev);
+    }
+    tick.ev = S->spare_events.back();
+    S->spare_events.pop_back();
+    st = cuda_status(cudaEventRecord(tick.ev, S->stream));
+    if (st)
+        return st;
+    S->inflight.push_back(std::move(tick));
+    ++S->n_ticks;
+    return RNG_OK;
+}
+
+bool has_active(const Server *S)
+{
+    for (const auto &a : S->active)
+        if (!a.empty())
+            return true;
+    return false;
+}
+
+int progress(Server *S)
+{
+    int st = retire(S);
+    if (st)
+        return st;
+    admit(S);
+    while ((int)S->inflight.size() < kMaxInflight && has_active(S)) {
+        st = launch_tick(S);
+        if (st)
+            return st;
+    }
+    return RNG_OK;
+}
+
+void free_server(Server *S)
+{
+    if (!S)
+        return;
+    if (S->stream)
+        cudaStreamSynchronize(S->stream);
+    rng_plan_destroy(S->plan);
+    for (rng_handle h : S->gens)
+        rng_destroy(h);
+    for (auto &t : S->inflight)
+        cudaEventDestroy(t.ev);
+    for (cudaEvent_t e : S->spare_events)
+        cudaEventDestroy(e);
+    if (S->t0)
+        cudaEventDestroy(S->t0);
+    if (S->stream)
+        cudaStreamDestroy(S->stream);
+    cudaFree(S->arena_base);
+    delete S->arena;
+    delete S;
+}
+
+}  // namespace
+}  // namespace gbrng
+
+using namespace gbrng;
+
+extern "C" rng_server_handle rng_server_create(int kind, uint32_t n_clients,
+                                               uint64_t streams_per_client, uint64_t seed_base,
+                                               uint64_t budget_bytes, uint32_t chunk_rows)
+{
+    if ((kind != RNG_MWC32 && kind != RNG_XOR128 && kind != RNG_KISS) || n_clients == 0 ||
+        streams_per_client == 0 || chunk_rows == 0 || streams_per_client >= (1ull << 32)) {
+        set_error(RNG_ERR_ARG);
+        return nullptr;
+    }
+    const uint64_t per_stream = 4ull * words_of(kind) + (kind != RNG_XOR128 ? 4 : 0);
+    const uint64_t state = per_stream * streams_per_client * n_clients;
+    if (state + (1 << 20) > budget_bytes) {
+        set_error(RNG_ERR_OOM);
+        return nullptr;
+    }
+    Server *S = new (std::nothrow) Server();
+    if (!S) {
+        set_error(RNG_ERR_OOM);
+        return nullptr;
+    }
+    S->kind = kind;
+    S->n_clients = n_clients;
+    S->streams = streams_per_client;
+    S->chunk_rows = chunk_rows;
+    cudaGetDevice(&S->device);
+    S->active.resize(n_clients);
+    S->cursor.assign(n_clients, 0);
+    // Seeds 2^32 apart: stream s of client k starts splitmix64 at
+    // seed_base + k * 2^32 + s, so no two streams of any clients share it.
+    for (uint32_t k = 0; k < n_clients; ++k) {
+        rng_handle h = rng_create(kind, streams_per_client, seed_base + ((uint64_t)k << 32));
+        if (!h) {
+            free_server(S);
+            return nullptr;
+        }
+        S->gens.push_back(h);
+    }
+    const uint64_t arena = (budget_bytes - state) / kGranule * kGranule;
+    int st = RNG_OK;
+    if (cudaMalloc(&S->arena_base, arena) != cudaSuccess)
+        st = set_error(RNG_ERR_OOM);
+    if (!st)
+        S->arena = new (std::nothrow) Arena(arena);
+    if (!st && !S->arena)
+        st = set_error(RNG_ERR_OOM);
+    if (!st)
+        st = cuda_status(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    if (!st)
+        st = cuda_status(cudaEventCreate(&S->t0));
+    if (!st)
+        st = cuda_status(cudaEventRecord(S->t0, S->stream));
+    for (rng_handle h : S->gens)
+        if (!st)
+            st = rng_set_stream(h, S->stream);
+    if (st) {
+        free_server(S);
+        return nullptr;
+    }
+    return reinterpret_cast<rng_server_handle>(S);
+}
+
+extern "C" int rng_server_submit(rng_server_handle h, uint32_t client, uint64_t n_samples,
+                                 int fmt, uint64_t *req_id)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || client >= S->n_clients || n_samples == 0 || (fmt != RNG_U32 && fmt != RNG_F32) ||
+        n_samples > S->arena->size() / 4)
+        return set_error(RNG_ERR_ARG);
+    const uint64_t id = S->next_id++;
+    Req q;
+    q.client = client;
+    q.n = n_samples;
+    q.fmt = fmt;
+    q.start = S->cursor[client];
+    S->cursor[client] += n_samples;
+    S->reqs.emplace(id, q);
+    S->pending.push_back(id);
+    if (req_id)
+        *req_id = id;
+    return RNG_OK;
+}
+
+extern "C" int rng_server_submit_many(rng_server_handle h, const uint32_t *clients,
+                                      const uint64_t *n_samples, const int *fmts, size_t n,
+                                      uint64_t *req_ids)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || (n && (!clients || !n_samples || !fmts)))
+        return set_error(RNG_ERR_ARG);
+    for (size_t i = 0; i < n; ++i)  // all or nothing
+        if (clients[i] >= S->n_clients || n_samples[i] == 0 ||
+            (fmts[i] != RNG_U32 && fmts[i] != RNG_F32) || n_samples[i] > S->arena->size() / 4)
+            return set_error(RNG_ERR_ARG);
+    for (size_t i = 0; i < n; ++i) {
+        int st = rng_server_submit(h, clients[i], n_samples[i], fmts[i], req_ids ? &req_ids[i]
+                                                                            : nullptr);
+        if (st)
+            return st;
+    }
+    return RNG_OK;
+}
+
+extern "C" int rng_server_progress(rng_server_handle h)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return set_error(RNG_ERR_ARG);
+    DeviceScope ds(S->device);
+    int st = progress(S);
+    return st ? st : (int)std::min<size_t>(S->done.size(), 0x7FFFFFFF);
+}
+
+extern "C" int rng_server_drain(rng_server_handle h)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return set_error(RNG_ERR_ARG);
+    DeviceScope ds(S->device);
+    for (;;) {
+        int st = progress(S);
+        if (st)
+            return st;
+        if (S->inflight.empty()) {
+            if (S->pending.empty() && !has_active(S))
+                return RNG_OK;
+            if (!has_active(S))
+                return set_error(RNG_ERR_BUSY);  // waiting requests need released space
+            continue;
+        }
+        cudaError_t e = cudaEventSynchronize(S->inflight.front().ev);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+    }
+}
+
+extern "C" int rng_server_take(rng_server_handle h, uint64_t *ids, double *done_ms, int cap)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || cap < 0 || (cap > 0 && !ids))
+        return set_error(RNG_ERR_ARG);
+    int n = 0;
+    while (n < cap && !S->done.empty()) {
+        ids[n] = S->done.front().first;
+        if (done_ms)
+            done_ms[n] = S->done.front().second;
+        S->done.pop_front();
+        ++n;
+    }
+    return n;
+}
+
+extern "C" int rng_server_result(rng_server_handle h, uint64_t req_id, void **dev_ptr,
+                                 uint64_t *n_samples, int *fmt, uint32_t *client, uint64_t *start)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return set_error(RNG_ERR_ARG);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end() || !it->second.completed)
+        return set_error(RNG_ERR_ARG);
+    const Req &q = it->second;
+    if (dev_ptr)
+        *dev_ptr = S->arena_base + q.off / 4;
+    if (n_samples)
+        *n_samples = q.n;
+    if (fmt)
+        *fmt = q.fmt;
+    if (client)
+        *client = q.client;
+    if (start)
+        *start = q.start;
+    return RNG_OK;
+}
+
+extern "C" int rng_server_copy(rng_server_handle h, uint64_t req_id, void *dst,
+                               uint64_t offset, uint64_t count, void *cuda_stream)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || !dst)
+        return set_error(RNG_ERR_ARG);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end() || !it->second.completed || offset > it->second.n ||
+        count > it->second.n - offset)
+        return set_error(RNG_ERR_ARG);
+    if (count == 0)
+        return RNG_OK;
+    DeviceScope ds(S->device);
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : S->stream;
+    const uint32_t *src = S->arena_base + it->second.off / 4 + offset;
+    return cuda_status(cudaMemcpyAsync(dst, src, count * 4, cudaMemcpyDefault, st));
+}
+
+extern "C" int rng_server_release(rng_server_handle h, uint64_t req_id)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return set_error(RNG_ERR_ARG);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end() || !it->second.completed)
+        return set_error(RNG_ERR_ARG);
+    S->arena->release(it->second.off, it->second.n * 4);
+    S->reqs.erase(it);
+    return RNG_OK;
+}
+
+extern "C" int rng_server_release_many(rng_server_handle h, const uint64_t *req_ids, size_t n)
+{
+    if (n && !req_ids)
+        return set_error(RNG_ERR_ARG);
+    int st = RNG_OK;
+    for (size_t i = 0; i < n; ++i) {
+        int e = rng_server_release(h, req_ids[i]);
+        if (e && !st)
+            st = e;
+    }
+    return st;
+}
+
+extern "C" int rng_server_stats(rng_server_handle h, uint64_t *out8)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || !out8)
+        return set_error(RNG_ERR_ARG);
+    out8[0] = S->next_id;
+    out8[1] = S->n_admitted;
+    out8[2] = S->n_completed;
+    out8[3] = S->n_ticks;
+    out8[4] = S->samples;
+    out8[5] = S->arena->used();
+    out8[6] = S->arena->size();
+    out8[7] = S->pending.size();
+    return RNG_OK;
+}
+
+extern "C" int rng_server_set_tick_bytes(rng_server_handle h, uint64_t bytes)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return set_error(RNG_ERR_ARG);
+    S->tick_bytes = bytes;
+    return RNG_OK;
+}
+
+extern "C" void *rng_server_stream(rng_server_handle h)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    return S ? static_cast<void *>(S->stream) : nullptr;
+}
+
+extern "C" void rng_server_destroy(rng_server_handle h)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S)
+        return;
+    DeviceScope ds(S->device);
+    free_server(S);
+}

@@ -184,6 +184,14 @@ class Plan:
         capi.check(capi.lib().rng_plan_shape(self.p, ctypes.byref(t), ctypes.byref(g)))
         return t.value, g.value
 
+    def refill(self, items: list[BatchItem], stream: torch.cuda.Stream | None = None) -> None:
+        """New work list for the next launch on `stream` (rng_plan_refill)."""
+        arr = _items(items)
+        capi.check(capi.lib().rng_plan_refill(self.p, arr, len(items),
+                                              ctypes.c_void_p(_stream_ptr(stream))),
+                   "rng_plan_refill")
+        self._keep = items
+
     def launch(self, stream: torch.cuda.Stream | None = None) -> None:
         capi.check(capi.lib().rng_plan_launch(self.p, ctypes.c_void_p(_stream_ptr(stream))),
                    "rng_plan_launch")
