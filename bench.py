@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other workloads (batched, serving, other configs)")
     p.add_argument("--workload", default="full", choices=["full", "batched", "serving"])
     p.add_argument("--rate", type=float, default=20_000.0, help="serving: arrivals/s")
     p.add_argument("--duration", type=float, default=10.0, help="serving: seconds")
@@ -60,7 +62,7 @@ def parse():
     p.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     p.add_argument("--ring", type=int, default=3, help="batched: waves in flight")
     p.add_argument("--no-verify", action="store_true", help="batched: skip the check pass")
-    p.add_argument("--chunk-rows", type=int, default=2048,
+    p.add_argument("--chunk-rows", type=int, default=1024,
                    help="batched: rows per piece (0 = whole instances)")
     return p.parse_args()
 
@@ -358,6 +360,12 @@ def run_ours(args):
                "steps": args.e2e_steps,
                "api": "rng_generate_host into pinned host memory"}
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        del gens
+        torch.cuda.empty_cache()
+        extras = run_extras(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(steps, 1 << 15)
@@ -377,6 +385,7 @@ def run_ours(args):
             "gpu_launches": args.steps * len(pairs), "clocks": clock_info,
             "per_kernel": per_kernel, "write_only_probe_gbs": write_only_gbs,
         }
+        line.update(extras)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -522,7 +531,7 @@ def run_batched(args):
                    "wave_bytes": budget, "graph": "one CUDA graph per wave",
                    "order": f"waves in order on one stream, {R} output buffers"},
     }
-    print(json.dumps(line))
+    return line
 
 
 # --------------------------------------------------------------- serving
@@ -632,7 +641,53 @@ def run_serving(args):
                    "chunk_rows": chunk_rows, "tick_bytes": int(args.tick_gib * (1 << 30)),
                    "seed_base": args.seed},
     }
-    print(json.dumps(line))
+    return line
+
+
+def _plain_rate(kind, n, steps, fmt, seed, reps=3):
+    import torch
+
+    from paper_1101_1846_gb300.generator import Generator
+    g = Generator(kind, n, seed)
+    out = torch.empty((steps, n), dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    g.generate(steps, fmt, out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        g.generate(steps, fmt, out=out)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    g.close()
+    ms = sorted(ts)[len(ts) // 2]
+    return {"ms": ms, "gsamples_s": n * steps / (ms * 1e-3) / 1e9}
+
+
+def run_extras(args):
+    """The other workloads, summarised for the same JSON line: the 2^20 x 1024
+    xor128/KISS calls, the 4096 x 4096 MWC call (few streams, latency-bound),
+    the batched 10,000-instance workload and the serving loop."""
+    extras = {"other_configs": {}}
+    for kind, kn in ((1, "xor128"), (2, "kiss")):
+        for fmt, fn in ((0, "u32"), (1, "f32")):
+            extras["other_configs"][f"{kn}_{fn}_2^20x1024"] = _plain_rate(kind, 1 << 20, 1024,
+                                                                          fmt, 7)
+    extras["other_configs"]["mwc_u32_4096x4096"] = _plain_rate(0, 4096, 4096, 0, 42)
+    keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
+            "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
+            "batched_ms", "gpu_launches")
+    args.tune = True  # pick the plan shape for this GPU (a few timed launches)
+    b = run_batched(args)
+    extras["batched"] = {k: b[k] for k in keep if k in b}
+    extras["batched"]["over_plain_full_device"] = None
+    s = run_serving(args)
+    extras["serving"] = {k: s[k] for k in ("value", "p50_ms", "p99_ms", "mean_ms", "requests",
+                                           "offered_gsamples_s", "saturating", "probe_checks",
+                                           "probe_mismatches", "bit_exact_probes", "config")}
+    return extras
 
 
 def main():
@@ -640,9 +695,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
-        run_batched(args)
+        print(json.dumps(run_batched(args)))
     elif args.workload == "serving":
-        run_serving(args)
+        print(json.dumps(run_serving(args)))
     else:
         run_ours(args)
 
