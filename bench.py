@@ -60,9 +60,10 @@ def parse():
     p.add_argument("--instances", type=int, default=10_000)
     p.add_argument("--wave-gib", type=float, default=24.0)
     p.add_argument("--tune", action="store_true", help="autotune launch shapes first")
-    p.add_argument("--ring", type=int, default=3, help="batched: waves in flight")
+    p.add_argument("--lanes", type=int, default=2,
+                   help="batched: groups of instances whose waves overlap")
     p.add_argument("--no-verify", action="store_true", help="batched: skip the check pass")
-    p.add_argument("--chunk-rows", type=int, default=1024,
+    p.add_argument("--chunk-rows", type=int, default=512,
                    help="batched: rows per piece (0 = whole instances)")
     return p.parse_args()
 
@@ -397,9 +398,10 @@ def run_batched(args):
     cut into pieces of at most --chunk-rows rows (the state carries from
     piece to piece, so the pieces give exactly the rows of one call), and
     the pieces are packed into waves of at most --wave-gib of output
-    (scheduler.chunked_waves).  Every wave is one plan (one persistent
-    kernel) captured in a CUDA graph; waves run on a ring of --ring streams
-    and buffers.  The same instances then run as plain per-instance
+    (scheduler.laned_waves: --lanes groups of instances, each with waves of
+    its own).  Every wave is one plan (one persistent kernel) captured in a
+    CUDA graph; a lane's waves run in order on its own stream, and the lanes
+    overlap.  The same instances then run as plain per-instance
     launches (timed), and a separate untimed pass checks every piece of
     every wave bit for bit against plain calls."""
     import torch
@@ -411,14 +413,17 @@ def run_batched(args):
     capi.lib()
     inst = workloads.batched_instances(args.instances, 1234)
     budget = int(args.wave_gib * (1 << 30))
-    waves = scheduler.chunked_waves([i.n_streams for i in inst],
-                                    [i.n_per_stream for i in inst], budget, args.chunk_rows)
-    R = max(2, args.ring)
+    lanes = max(1, args.lanes)
+    laned = scheduler.laned_waves([i.n_streams for i in inst], [i.n_per_stream for i in inst],
+                                  budget, args.chunk_rows, lanes)
+    waves = [w for _, w in laned]
     main = torch.cuda.current_stream()
-    # Consecutive waves hold consecutive pieces of the same instances, so the
-    # waves run in order on one stream; the R buffers only alternate.
-    streams = [torch.cuda.Stream()]
-    longest = max(4 * i.n_streams * i.n_per_stream for i in inst)
+    # A lane's waves continue the same instances, so they run in order on the
+    # lane's stream and reuse the lane's buffer; lanes share no instance and
+    # overlap.  The check pass below needs two buffers.
+    streams = [torch.cuda.Stream() for _ in range(lanes)]
+    R = max(2, lanes)
+    longest = max(4 * i.n_streams * i.n_per_stream for i in inst)  # plain calls write whole
     cap = max(budget, longest) // 4 + 4 * max(len(w) for w in waves)
     bufs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(R)]
 
@@ -449,11 +454,11 @@ def run_batched(args):
 
     # plans and graphs for every wave, built before the timed region
     plans, graphs, tiles = [], [], 0
-    for k, w in enumerate(waves):
-        plan = Plan(items_for(gb, w, carve(bufs[k % R], w)), threads=shape[0],
+    for lane, w in laned:
+        plan = Plan(items_for(gb, w, carve(bufs[lane], w)), threads=shape[0],
                     ctas_per_sm=shape[1])
         tiles += plan.tiles
-        s = streams[0]
+        s = streams[lane]
         s.wait_stream(main)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=s):
@@ -467,8 +472,8 @@ def run_batched(args):
     e0.record(main)
     for s in streams:
         s.wait_stream(main)
-    with torch.cuda.stream(streams[0]):
-        for graph in graphs:
+    for (lane, _), graph in zip(laned, graphs):
+        with torch.cuda.stream(streams[lane]):
             graph.replay()
     for s in streams:
         main.wait_stream(s)
@@ -520,7 +525,7 @@ def run_batched(args):
         "plain_per_instance_value": samples / (p_ms * 1e-3) / 1e9,
         "batched_over_plain_per_instance": p_ms / b_ms, "samples": samples,
         "bytes": 4 * samples, "waves": len(waves), "pieces": sum(len(w) for w in waves),
-        "ring": R, "tiles": tiles, "chunk_rows": args.chunk_rows,
+        "lanes": lanes, "tiles": tiles, "chunk_rows": args.chunk_rows,
         "batched_ms": b_ms, "plain_ms": p_ms, "plain_launches": len(inst),
         "gpu_launches": len(waves), "plan_shape": list(shape), "tune_ms":
             {f"{t}x{c}": v for (t, c), v in tune_ms.items()} if tune_ms else None,
@@ -529,7 +534,8 @@ def run_batched(args):
         "realigned_instances": sum(1 for i in inst if i.n_streams % 4),
         "config": {"workload": "batched", "instances": args.instances, "seed": 1234,
                    "wave_bytes": budget, "graph": "one CUDA graph per wave",
-                   "order": f"waves in order on one stream, {R} output buffers"},
+                   "order": f"{lanes} lanes: a lane's waves in order on its own stream "
+                            "and buffer, lanes overlapping"},
     }
     return line
 
@@ -594,15 +600,16 @@ def run_serving(args):
             return
         srv = active[0]
         info = srv.result(rid)
-        out = srv.copy(rid)
         start, N = info["start"], info["n"]
+        out = srv.copy(rid, out=torch.empty(N, dtype=torch.int32, pin_memory=True))
+        out = out.numpy().view(np.uint32)
         for s in probes:
             col = (s - start) % streams
             if col >= N:
                 continue
             cnt = (N - 1 - col) // streams + 1
-            pos = torch.arange(cnt, device="cuda", dtype=torch.int64) * streams + col
-            got = out[pos].cpu().numpy().view(np.uint32)
+            got = out[col::streams]
+            assert len(got) == cnt
             row0 = (start + col) // streams
             u, f = seqs[(info["client"], s)]
             exp = (u if info["fmt"] == 0 else f)[row0:row0 + cnt]

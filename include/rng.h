@@ -253,8 +253,9 @@ int rng_generate_batch(const rng_batch_item *items, size_t n_items,
  * state), and on every tick runs one batched launch (a refilled plan) that
  * advances every client with admitted work by one piece of at most
  * chunk_rows rows of its current request: requests that arrive while others
- * run join the next tick (continuous batching).  Up to two ticks are in
- * flight on the engine's own CUDA stream.  A request's output (uint32 or
+ * run join the next tick (continuous batching).  Clients are split into two
+ * lanes (even and odd ids) with a CUDA stream each, so that one lane's tick
+ * overlaps the other's; up to two ticks per lane are in flight.  A request's output (uint32 or
  * float, N elements, contiguous, in sequence order) stays in the arena until
  * it is released.  Not thread-safe: drive one engine from one host thread.
  * Paper: none; the parametrised generators of Sec. "Parallelizing RNGs"
@@ -306,8 +307,12 @@ int rng_server_result(rng_server_handle s, uint64_t req_id, void **dev_ptr,
                       uint64_t *n_samples, int *fmt, uint32_t *client, uint64_t *start);
 
 /* Copies elements [offset, offset + count) of a completed request's output
- * to dst (device or host memory) on cuda_stream (NULL: the engine's
- * stream).  Asynchronous; release the request only after the copy is done. */
+ * to dst (device or host memory) on cuda_stream, a cudaStream_t (NULL: the
+ * legacy default stream, as everywhere in this library).  The tick that
+ * produced a completed request has finished, so any stream may be used.
+ * Asynchronous: the caller synchronises cuda_stream (or orders its own work
+ * after the copy on it), and releases the request only after the copy is
+ * done. */
 int rng_server_copy(rng_server_handle s, uint64_t req_id, void *dst, uint64_t offset,
                     uint64_t count, void *cuda_stream);
 
@@ -329,10 +334,6 @@ int rng_server_stats(rng_server_handle s, uint64_t *out8);
  * a backlog (throughput).  0 (the default) gives every client chunk_rows
  * rows per tick. */
 int rng_server_set_tick_bytes(rng_server_handle s, uint64_t bytes);
-
-/* The engine's CUDA stream (a cudaStream_t), e.g. to order a copy of a
- * result after the tick that produced it. */
-void *rng_server_stream(rng_server_handle s);
 
 /* Waits for the engine's work and frees everything.  NULL is ignored. */
 void rng_server_destroy(rng_server_handle s);

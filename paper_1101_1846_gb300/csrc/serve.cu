@@ -1,6 +1,8 @@
 // Serving engine: device-resident client generators, an output arena under
 // an HBM budget, FIFO admission and continuous batching.  See the contract in
-// include/rng.h (rng_server_*).
+// include/rng.h (rng_server_*).  Clients are split into two lanes (even and
+// odd ids), each with its own stream, plan and ticks, so that one lane's
+// tick overlaps the other's instead of waiting for its last tiles.
 //
 // Sample g of a client's sequence is output g / n of stream g % n (n streams
 // per client).  A piece of m samples starting at sample c covers columns
@@ -22,7 +24,8 @@ namespace gbrng {
 namespace {
 
 constexpr uint64_t kGranule = 256;  // arena alignment, bytes
-constexpr int kMaxInflight = 2;
+constexpr int kMaxInflight = 2;     // ticks in flight per lane
+constexpr int kLanes = 2;           // client c belongs to lane c % kLanes
 constexpr int kServeThreads = 512;
 
 // First-fit allocator over [0, size) bytes in kGranule units.
@@ -107,14 +110,14 @@ struct Server {
     std::deque<uint64_t> pending;                 // waiting for admission
     std::vector<std::deque<uint64_t>> active;     // admitted, per client, in order
     std::unordered_map<uint64_t, Req> reqs;
-    std::deque<Tick> inflight;
+    std::deque<Tick> inflight[kLanes];
     std::vector<cudaEvent_t> spare_events;
     std::deque<std::pair<uint64_t, double>> done;  // completed, not yet taken
     std::vector<rng_batch_item> items;
-    rng_plan_handle plan = nullptr;
-    cudaStream_t stream = nullptr;
+    rng_plan_handle plan[kLanes] = {};
+    cudaStream_t stream[kLanes] = {};
     cudaEvent_t t0 = nullptr;
-    uint32_t rr = 0;  // round-robin start client
+    uint32_t rr[kLanes] = {};  // round-robin start, per lane
     uint64_t tick_bytes = 0;  // target output per tick (0: chunk_rows alone)
     uint64_t next_id = 0, n_admitted = 0, n_completed = 0, n_ticks = 0, samples = 0;
 };
@@ -157,24 +160,26 @@ void piece_items(rng_handle h, uint64_t n, uint64_t c, uint64_t m, uint32_t *out
 
 int retire(Server *S)
 {
-    while (!S->inflight.empty()) {
-        Tick &t = S->inflight.front();
-        cudaError_t e = cudaEventQuery(t.ev);
-        if (e == cudaErrorNotReady)
-            break;
-        if (e != cudaSuccess)
-            return cuda_status(e);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, S->t0, t.ev);
-        for (uint64_t id : t.completing) {
-            Req &q = S->reqs[id];
-            q.completed = true;
-            q.done_ms = ms;
-            S->done.emplace_back(id, (double)ms);
-            ++S->n_completed;
+    for (int ln = 0; ln < kLanes; ++ln) {
+        while (!S->inflight[ln].empty()) {
+            Tick &t = S->inflight[ln].front();
+            cudaError_t e = cudaEventQuery(t.ev);
+            if (e == cudaErrorNotReady)
+                break;
+            if (e != cudaSuccess)
+                return cuda_status(e);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, S->t0, t.ev);
+            for (uint64_t id : t.completing) {
+                Req &q = S->reqs[id];
+                q.completed = true;
+                q.done_ms = ms;
+                S->done.emplace_back(id, (double)ms);
+                ++S->n_completed;
+            }
+            S->spare_events.push_back(t.ev);
+            S->inflight[ln].pop_front();
         }
-        S->spare_events.push_back(t.ev);
-        S->inflight.pop_front();
     }
     return RNG_OK;
 }
@@ -194,7 +199,9 @@ void admit(Server *S)
     }
 }
 
-int launch_tick(Server *S)
+// One tick of `lane`: one piece of every busy client of the lane, one launch
+// on the lane's stream.
+int launch_tick(Server *S, int lane)
 {
     S->items.clear();
     Tick tick;
@@ -202,14 +209,15 @@ int launch_tick(Server *S)
     if (S->tick_bytes) {
         // an equal share of the target tick for every client with work
         uint64_t busy = 0;
-        for (const auto &a : S->active)
-            busy += !a.empty();
+        for (uint32_t c = lane; c < S->n_clients; c += kLanes)
+            busy += !S->active[c].empty();
         const uint64_t share = busy ? S->tick_bytes / (busy * S->streams * 4) : rows;
         rows = std::max<uint64_t>(1, std::min<uint64_t>(rows, share));
     }
     const uint64_t cap = rows * S->streams;
-    for (uint32_t k = 0; k < S->n_clients; ++k) {
-        const uint32_t c = (S->rr + k) % S->n_clients;
+    const uint32_t per_lane = (S->n_clients - lane + kLanes - 1) / kLanes;
+    for (uint32_t k = 0; k < per_lane; ++k) {
+        const uint32_t c = lane + kLanes * ((S->rr[lane] + k) % per_lane);
         if (S->active[c].empty())
             continue;
         const uint64_t id = S->active[c].front();
@@ -224,18 +232,19 @@ int launch_tick(Server *S)
             S->active[c].pop_front();
         }
     }
-    S->rr = (S->rr + 1) % S->n_clients;
+    if (per_lane)
+        S->rr[lane] = (S->rr[lane] + 1) % per_lane;
     if (S->items.empty())
         return RNG_OK;
     int st;
-    if (!S->plan) {
-        S->plan = rng_plan_create(S->items.data(), S->items.size(), kServeThreads, 0);
-        st = S->plan ? RNG_OK : rng_last_error();
+    if (!S->plan[lane]) {
+        S->plan[lane] = rng_plan_create(S->items.data(), S->items.size(), kServeThreads, 0);
+        st = S->plan[lane] ? RNG_OK : rng_last_error();
     } else {
-        st = rng_plan_refill(S->plan, S->items.data(), S->items.size(), S->stream);
+        st = rng_plan_refill(S->plan[lane], S->items.data(), S->items.size(), S->stream[lane]);
     }
     if (!st)
-        st = rng_plan_launch(S->plan, S->stream);
+        st = rng_plan_launch(S->plan[lane], S->stream[lane]);
     if (st)
         return st;
     if (S->spare_events.empty()) {
@@ -246,18 +255,34 @@ int launch_tick(Server *S)
     }
     tick.ev = S->spare_events.back();
     S->spare_events.pop_back();
-    st = cuda_status(cudaEventRecord(tick.ev, S->stream));
+    st = cuda_status(cudaEventRecord(tick.ev, S->stream[lane]));
     if (st)
         return st;
-    S->inflight.push_back(std::move(tick));
+    S->inflight[lane].push_back(std::move(tick));
     ++S->n_ticks;
     return RNG_OK;
 }
 
+bool lane_active(const Server *S, int lane)
+{
+    for (uint32_t c = lane; c < S->n_clients; c += kLanes)
+        if (!S->active[c].empty())
+            return true;
+    return false;
+}
+
 bool has_active(const Server *S)
 {
-    for (const auto &a : S->active)
-        if (!a.empty())
+    for (int ln = 0; ln < kLanes; ++ln)
+        if (lane_active(S, ln))
+            return true;
+    return false;
+}
+
+bool any_inflight(const Server *S)
+{
+    for (int ln = 0; ln < kLanes; ++ln)
+        if (!S->inflight[ln].empty())
             return true;
     return false;
 }
@@ -268,10 +293,12 @@ int progress(Server *S)
     if (st)
         return st;
     admit(S);
-    while ((int)S->inflight.size() < kMaxInflight && has_active(S)) {
-        st = launch_tick(S);
-        if (st)
-            return st;
+    for (int ln = 0; ln < kLanes; ++ln) {
+        while ((int)S->inflight[ln].size() < kMaxInflight && lane_active(S, ln)) {
+            st = launch_tick(S, ln);
+            if (st)
+                return st;
+        }
     }
     return RNG_OK;
 }
@@ -280,19 +307,23 @@ void free_server(Server *S)
 {
     if (!S)
         return;
-    if (S->stream)
-        cudaStreamSynchronize(S->stream);
-    rng_plan_destroy(S->plan);
+    for (int ln = 0; ln < kLanes; ++ln)
+        if (S->stream[ln])
+            cudaStreamSynchronize(S->stream[ln]);
+    for (int ln = 0; ln < kLanes; ++ln)
+        rng_plan_destroy(S->plan[ln]);
     for (rng_handle h : S->gens)
         rng_destroy(h);
-    for (auto &t : S->inflight)
-        cudaEventDestroy(t.ev);
+    for (int ln = 0; ln < kLanes; ++ln)
+        for (auto &t : S->inflight[ln])
+            cudaEventDestroy(t.ev);
     for (cudaEvent_t e : S->spare_events)
         cudaEventDestroy(e);
     if (S->t0)
         cudaEventDestroy(S->t0);
-    if (S->stream)
-        cudaStreamDestroy(S->stream);
+    for (int ln = 0; ln < kLanes; ++ln)
+        if (S->stream[ln])
+            cudaStreamDestroy(S->stream[ln]);
     cudaFree(S->arena_base);
     delete S->arena;
     delete S;
@@ -348,15 +379,16 @@ extern "C" rng_server_handle rng_server_create(int kind, uint32_t n_clients,
         S->arena = new (std::nothrow) Arena(arena);
     if (!st && !S->arena)
         st = set_error(RNG_ERR_OOM);
-    if (!st)
-        st = cuda_status(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    for (int ln = 0; ln < kLanes && !st; ++ln)
+        st = cuda_status(cudaStreamCreateWithFlags(&S->stream[ln], cudaStreamNonBlocking));
     if (!st)
         st = cuda_status(cudaEventCreate(&S->t0));
     if (!st)
-        st = cuda_status(cudaEventRecord(S->t0, S->stream));
-    for (rng_handle h : S->gens)
-        if (!st)
-            st = rng_set_stream(h, S->stream);
+        st = cuda_status(cudaEventRecord(S->t0, S->stream[0]));
+    if (!st)
+        st = cuda_status(cudaEventSynchronize(S->t0));
+    for (uint32_t k = 0; k < n_clients && !st; ++k)
+        st = rng_set_stream(S->gens[k], S->stream[k % kLanes]);
     if (st) {
         free_server(S);
         return nullptr;
@@ -425,16 +457,21 @@ extern "C" int rng_server_drain(rng_server_handle h)
         int st = progress(S);
         if (st)
             return st;
-        if (S->inflight.empty()) {
+        if (!any_inflight(S)) {
             if (S->pending.empty() && !has_active(S))
                 return RNG_OK;
             if (!has_active(S))
                 return set_error(RNG_ERR_BUSY);  // waiting requests need released space
             continue;
         }
-        cudaError_t e = cudaEventSynchronize(S->inflight.front().ev);
-        if (e != cudaSuccess)
-            return cuda_status(e);
+        for (int ln = 0; ln < kLanes; ++ln) {
+            if (S->inflight[ln].empty())
+                continue;
+            cudaError_t e = cudaEventSynchronize(S->inflight[ln].front().ev);
+            if (e != cudaSuccess)
+                return cuda_status(e);
+            break;
+        }
     }
 }
 
@@ -490,7 +527,8 @@ extern "C" int rng_server_copy(rng_server_handle h, uint64_t req_id, void *dst,
     if (count == 0)
         return RNG_OK;
     DeviceScope ds(S->device);
-    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : S->stream;
+    // a completed request's tick has finished: any stream may copy it
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const uint32_t *src = S->arena_base + it->second.off / 4 + offset;
     return cuda_status(cudaMemcpyAsync(dst, src, count * 4, cudaMemcpyDefault, st));
 }
@@ -544,12 +582,6 @@ extern "C" int rng_server_set_tick_bytes(rng_server_handle h, uint64_t bytes)
         return set_error(RNG_ERR_ARG);
     S->tick_bytes = bytes;
     return RNG_OK;
-}
-
-extern "C" void *rng_server_stream(rng_server_handle h)
-{
-    Server *S = reinterpret_cast<Server *>(h);
-    return S ? static_cast<void *>(S->stream) : nullptr;
 }
 
 extern "C" void rng_server_destroy(rng_server_handle h)

@@ -10,7 +10,10 @@ launch does not wait on a few long dependency chains.
 chunked_waves() builds the waves: each wave takes the next piece of as many
 active instances as fit in a byte budget, in round-robin order, with at most
 one piece per instance (two pieces of one generator in the same launch would
-advance the same streams twice).
+advance the same streams twice).  laned_waves() splits the instances into
+lanes with waves of their own and interleaves them: waves of one lane must
+run in order, waves of different lanes share no instance and may overlap, so
+a wave's last tiles run beside the next lane's wave.
 """
 from __future__ import annotations
 
@@ -58,3 +61,24 @@ def chunked_waves(streams: list[int], rows: list[int], budget_bytes: int,
         queue.extend(deferred)
         waves.append(wave)
     return waves
+
+
+def laned_waves(streams: list[int], rows: list[int], budget_bytes: int, chunk_rows: int,
+                lanes: int = 2, elem_bytes: int = 4) -> list[tuple[int, list[Piece]]]:
+    """(lane, wave) pairs, lanes interleaved round-robin.  Instance i belongs
+    to lane i % lanes; each lane's waves are chunked_waves() of its own
+    instances (with their original indices) under the same budget."""
+    per_lane = []
+    for ln in range(lanes):
+        idx = list(range(ln, len(streams), lanes))
+        waves = chunked_waves([streams[i] for i in idx], [rows[i] for i in idx], budget_bytes,
+                              chunk_rows, elem_bytes)
+        per_lane.append([[Piece(idx[p.inst], p.row0, p.rows) for p in w] for w in waves])
+    out = []
+    k = 0
+    while any(k < len(w) for w in per_lane):
+        for ln in range(lanes):
+            if k < len(per_lane[ln]):
+                out.append((ln, per_lane[ln][k]))
+        k += 1
+    return out

@@ -91,14 +91,17 @@ class Server:
     def copy(self, rid: int, offset: int = 0, count: int | None = None,
              out: torch.Tensor | None = None) -> torch.Tensor:
         """The request's output (or a slice) as an int32 tensor on the device
-        (float requests hold float bits); synchronises the engine's stream."""
+        (float requests hold float bits); synchronises torch's current stream."""
         info = self.result(rid)
         count = info["n"] - offset if count is None else count
         if out is None:
             out = torch.empty(count, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
         capi.check(capi.lib().rng_server_copy(self.h, rid, ctypes.c_void_p(out.data_ptr()),
-                                              offset, count, None), "rng_server_copy")
-        torch.cuda.ExternalStream(capi.lib().rng_server_stream(self.h)).synchronize()
+                                              offset, count,
+                                              ctypes.c_void_p(stream.cuda_stream)),
+                   "rng_server_copy")
+        stream.synchronize()
         return out
 
     def release(self, rid: int) -> None:

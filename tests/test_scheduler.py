@@ -45,3 +45,21 @@ def test_batched_workload_waves_fit():
 def test_oversized_piece_alone():
     waves = check([1000, 10], [100, 5], 4 * 1000 * 10, 0)
     assert len(waves[0]) == 1 and waves[0][0].inst == 0
+
+
+def test_laned_waves_keep_each_instance_in_one_lane_and_in_order():
+    rng = np.random.Generator(np.random.PCG64(8))
+    streams = rng.integers(1, 3000, 200).tolist()
+    rows = rng.integers(1, 5000, 200).tolist()
+    waves = scheduler.laned_waves(streams, rows, 32 << 20, 300, lanes=2)
+    covered = [0] * len(streams)
+    lane_of = {}
+    for lane, w in waves:
+        assert sum(4 * streams[p.inst] * p.rows for p in w) <= 32 << 20 or len(w) == 1
+        for p in w:
+            assert lane_of.setdefault(p.inst, lane) == lane == p.inst % 2
+            assert p.row0 == covered[p.inst]
+            covered[p.inst] += p.rows
+    assert covered == rows
+    lanes = [lane for lane, _ in waves]
+    assert lanes[:4] == [0, 1, 0, 1]

@@ -181,3 +181,26 @@ def test_submit_many_and_release_many():
         s.submit_many(np.array([0, clients]), np.array([5, 5]), np.array([0, 0]))
     assert s.stats()["submitted"] == len(log)
     s.close()
+
+
+def test_copy_on_user_stream_and_to_host():
+    """rng_server_copy enqueues on the stream it is given: torch's current
+    stream (a side stream here), or pinned host memory as the target."""
+    n, clients = 300, 2
+    log = make_log(8, clients, 4000, seed=5)
+    s = Server(capi.RNG_KISS, clients, n, seed_base=9, budget_bytes=16 << 20, chunk_rows=3)
+    rids = [s.submit(r.client, r.n_samples, r.fmt) for r in log]
+    s.drain()
+    s.take()
+    side = torch.cuda.Stream()
+    outs = {}
+    for i, rid in enumerate(rids):
+        with torch.cuda.stream(side):
+            dev = s.copy(rid)
+        host = s.copy(rid, out=torch.empty(log[i].n_samples, dtype=torch.int32,
+                                           pin_memory=True))
+        assert torch.equal(dev.cpu(), host)
+        outs[i] = (s.result(rid), host.numpy().view(np.uint32))
+    check_against_oracle(s, log, outs, oracle.KISS, n)
+    s.release_many(np.array(rids))
+    s.close()
