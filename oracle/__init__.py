@@ -104,6 +104,15 @@ def _load(path: Path):
         "oracle_stream": (None, [i32, u32, _u32p, u64, i32, ctypes.c_void_p]),
         "oracle_generate": (None, [i32, u64, _u32p, _u32p, u64, i32,
                                    ctypes.c_void_p]),
+        "oracle_sum_u32": (u64, [_u32p, u64]),
+        "oracle_sum_u24": (u64, [_u32p, u64]),
+        "oracle_disc_count": (u64, [_u32p, u64]),
+        "oracle_reduce": (i32, [i32, u64, _u32p, _u32p, u64, i32, _u64p]),
+        "oracle_mwc_jump": (None, [u32, _u32p, _u32p, u64, i32]),
+        "oracle_xor128_jump": (None, [_u32p, u64]),
+        "oracle_xorshift32_jump": (None, [_u32p, u64]),
+        "oracle_lcg_jump": (None, [_u32p, u64]),
+        "oracle_jump": (None, [i32, u32, _u32p, u64]),
         "oracle_mwc_period": (u64, [u32, u32, u32, i32, u64]),
         "oracle_xorshift32_period": (u64, [u32]),
         "oracle_lcg_period": (u64, [u32]),
@@ -272,6 +281,75 @@ def stream(kind: int, a: int, st, n: int, fmt: int) -> tuple[np.ndarray, np.ndar
     lib().oracle_stream(kind, a, _p32(arr), n, fmt,
                         out.ctypes.data_as(ctypes.c_void_p))
     return out, arr
+
+
+# ------------------------------------------------------------ consumers
+SUM_U32, SUM_U24, DISC = 0, 1, 2
+
+
+def sum_u32(u: np.ndarray) -> int:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    return int(lib().oracle_sum_u32(_p32(u), len(u)))
+
+
+def sum_u24(u: np.ndarray) -> int:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    return int(lib().oracle_sum_u24(_p32(u), len(u)))
+
+
+def disc_count(u: np.ndarray) -> int:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    return int(lib().oracle_disc_count(_p32(u), len(u)))
+
+
+def reduce(kind: int, a: np.ndarray | None, state: np.ndarray, n_per_stream: int,
+           op: int) -> tuple[np.ndarray, np.ndarray]:
+    """Every stream advances n_per_stream steps; returns (out, new_state)
+    with out[s] the consumer `op` over stream s's outputs (uint64)."""
+    state = np.array(state, dtype=np.uint32, order="C", copy=True)
+    n = state.shape[0]
+    out = np.zeros(n, np.uint64)
+    ap = None
+    if kind != XOR128:
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+        assert len(a) >= n
+        ap = _p32(a)
+    rc = lib().oracle_reduce(kind, n, ap, _p32(state), n_per_stream, op, _p64(out))
+    assert rc == 0, "oracle_reduce: out of memory"
+    return out, state
+
+
+# ----------------------------------------------------------------- jumps
+def jump(kind: int, a: int, st, k: int) -> np.ndarray:
+    """State of one stream k steps after st (4 uint32 words)."""
+    arr = np.array(st, dtype=np.uint32)
+    lib().oracle_jump(kind, int(a), _p32(arr), int(k))
+    return arr
+
+
+def jump_streams(kind: int, a: np.ndarray | None, state: np.ndarray, k: int) -> np.ndarray:
+    out = np.array(state, dtype=np.uint32, order="C", copy=True)
+    for s in range(out.shape[0]):
+        lib().oracle_jump(kind, int(a[s]) if a is not None else 0, _p32(out[s]), int(k))
+    return out
+
+
+def mwc_jump(a: int, x: int, c: int, k: int, log2b: int = 32) -> tuple[int, int]:
+    X, C = ctypes.c_uint32(x), ctypes.c_uint32(c)
+    lib().oracle_mwc_jump(a, ctypes.byref(X), ctypes.byref(C), k, log2b)
+    return int(X.value), int(C.value)
+
+
+def xorshift32_jump(y: int, k: int) -> int:
+    Y = ctypes.c_uint32(y)
+    lib().oracle_xorshift32_jump(ctypes.byref(Y), k)
+    return int(Y.value)
+
+
+def lcg_jump(z: int, k: int) -> int:
+    Z = ctypes.c_uint32(z)
+    lib().oracle_lcg_jump(ctypes.byref(Z), k)
+    return int(Z.value)
 
 
 # ---------------------------------------------------------------- periods

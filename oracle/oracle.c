@@ -22,9 +22,15 @@
  *   splitmix64 seeding ............. increment pinned (golden ratio); the
  *                                    finaliser constants are parity unpinned
  *                                    beyond a published test value
+ *   consumers (sums, disc count) ... pinned (closed-form sums of synthetic
+ *                                    sequences; lattice count of the quarter
+ *                                    disc by integer square roots)
+ *   jump-ahead ..................... pinned (equal to stepping; periods of
+ *                                    each part reached by one jump)
  */
 #include "oracle.h"
 
+#include <stdlib.h>
 #include <string.h>
 
 /* ------------------------------------------------------------------ */
@@ -405,4 +411,222 @@ void oracle_seed_streams(int kind, const uint32_t *a, uint64_t seed,
 {
     for (uint64_t i = 0; i < n; ++i)
         oracle_seed_stream(kind, a ? a[i] : 0, seed, s_ids[i], st + 4 * i);
+}
+
+/* ------------------------------------------------------------------ */
+/* Consumers with no output array.  The paper also times its generators
+ * with the numbers kept on chip and only the final state stored, the case
+ * of an application that calls the generator inline (Sec. "Performance
+ * evaluation"; the "without writeback" rows of Tables I-III).  Here each
+ * consumer reads one stream's outputs in order and reduces them to one
+ * 64-bit number, so that every output is used.                          */
+/* ------------------------------------------------------------------ */
+
+/* Sum of the outputs, mod 2^64. */
+uint64_t oracle_sum_u32(const uint32_t *u, uint64_t n)
+{
+    uint64_t s = 0;
+    for (uint64_t j = 0; j < n; ++j)
+        s += (uint64_t)u[j];
+    return s;
+}
+
+/* Sum of the 24-bit integers u >> 8: exactly 2^24 times the sum of the
+ * float32 uniforms of the same outputs. */
+uint64_t oracle_sum_u24(const uint32_t *u, uint64_t n)
+{
+    uint64_t s = 0;
+    for (uint64_t j = 0; j < n; ++j)
+        s += (uint64_t)(u[j] >> 8);
+    return s;
+}
+
+/* Consecutive outputs taken two at a time, (u[2k], u[2k+1]) for
+ * k < floor(n / 2), as the point (x, y) of their float32 uniforms: the
+ * number of points with x^2 + y^2 < 1.  With x = X 2^-24 and y = Y 2^-24
+ * the test is X^2 + Y^2 < 2^48, evaluated exactly in integers.  The count
+ * over P points estimates P pi / 4. */
+uint64_t oracle_disc_count(const uint32_t *u, uint64_t n)
+{
+    uint64_t inside = 0;
+    for (uint64_t k = 0; 2 * k + 1 < n; ++k) {
+        uint64_t X = u[2 * k] >> 8;
+        uint64_t Y = u[2 * k + 1] >> 8;
+        if (X * X + Y * Y < ((uint64_t)1 << 48))
+            ++inside;
+    }
+    return inside;
+}
+
+/* Every stream advances n_per_stream steps (state in place, 4 words per
+ * stream as in oracle_generate); out[s] is the chosen consumer applied to
+ * stream s's outputs: op 0 = oracle_sum_u32, 1 = oracle_sum_u24,
+ * 2 = oracle_disc_count.  Returns 0, or -1 if the scratch row cannot be
+ * allocated. */
+int oracle_reduce(int kind, uint64_t n_streams, const uint32_t *a,
+                  uint32_t *state, uint64_t n_per_stream, int op,
+                  uint64_t *out)
+{
+    uint32_t *row = (uint32_t *)malloc((n_per_stream ? n_per_stream : 1) * sizeof(uint32_t));
+    if (!row)
+        return -1;
+    for (uint64_t s = 0; s < n_streams; ++s) {
+        oracle_stream(kind, a ? a[s] : 0, state + 4 * s, n_per_stream, 0, row);
+        if (op == 0)
+            out[s] = oracle_sum_u32(row, n_per_stream);
+        else if (op == 1)
+            out[s] = oracle_sum_u24(row, n_per_stream);
+        else
+            out[s] = oracle_disc_count(row, n_per_stream);
+    }
+    free(row);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Jump-ahead: the state k steps later, computed without the steps in
+ * between.  Sequence splitting needs it (Sec. "Parallelizing RNGs": a
+ * node starts where the previous node's block of numbers ends).          */
+/* ------------------------------------------------------------------ */
+
+/* MWC, b = 2^log2b, p = a b - 1.  With t = a x + c (0 < t < p for every
+ * state except the two fixed points), one step gives
+ *   x' = t mod b,  c' = t div b,  t' = a x' + c',
+ * and b t' = a b (t mod b) + t - (t mod b) = t + p (t mod b), so
+ * t' = b^-1 t = a t (mod p) because a b = 1 (mod p).  Hence k steps
+ * multiply t by a^k mod p, and (x, c) is recovered from t as
+ * x = t div a, c = t mod a (the state keeps 0 <= c < a). */
+void oracle_mwc_jump(uint32_t a, uint32_t *x, uint32_t *c, uint64_t k,
+                     int log2b)
+{
+    uint64_t p = (uint64_t)a * ((uint64_t)1 << log2b) - 1;
+    uint64_t t = (uint64_t)(*c) + (uint64_t)(*x) * a;
+    t = oracle_mulmod_u64(oracle_powmod_u64(a, k, p), t, p);
+    *x = (uint32_t)(t / a);
+    *c = (uint32_t)(t % a);
+}
+
+/* GF(2) matrices of at most 128 x 128 bits.  Bit i of a state vector is
+ * bit (i mod 32) of word i / 32.  Column j of the matrix of a linear step
+ * is the image of the unit vector e_j under the step. */
+typedef struct {
+    int nbits;
+    uint32_t col[128][4];
+} gf2mat;
+
+static void gf2_apply(const gf2mat *m, const uint32_t v[4], uint32_t out[4])
+{
+    uint32_t r[4] = {0, 0, 0, 0};
+    for (int j = 0; j < m->nbits; ++j) {
+        if ((v[j / 32] >> (j % 32)) & 1u) {
+            for (int w = 0; w < 4; ++w)
+                r[w] ^= m->col[j][w];
+        }
+    }
+    memcpy(out, r, sizeof(r));
+}
+
+/* out = a * b: column j of the product is a applied to column j of b. */
+static void gf2_mul(const gf2mat *a, const gf2mat *b, gf2mat *out)
+{
+    gf2mat r;
+    r.nbits = a->nbits;
+    for (int j = 0; j < a->nbits; ++j)
+        gf2_apply(a, b->col[j], r.col[j]);
+    *out = r;
+}
+
+static void gf2_identity(gf2mat *m, int nbits)
+{
+    memset(m, 0, sizeof(*m));
+    m->nbits = nbits;
+    for (int j = 0; j < nbits; ++j)
+        m->col[j][j / 32] = 1u << (j % 32);
+}
+
+/* m^k by binary powering. */
+static void gf2_pow(const gf2mat *m, uint64_t k, gf2mat *out)
+{
+    gf2mat result, base = *m;
+    gf2_identity(&result, m->nbits);
+    while (k) {
+        if (k & 1)
+            gf2_mul(&result, &base, &result);
+        gf2_mul(&base, &base, &base);
+        k >>= 1;
+    }
+    *out = result;
+}
+
+static void xor128_matrix(gf2mat *m)
+{
+    memset(m, 0, sizeof(*m));
+    m->nbits = 128;
+    for (int j = 0; j < 128; ++j) {
+        uint32_t st[4] = {0, 0, 0, 0};
+        st[j / 32] = 1u << (j % 32);
+        oracle_xor128_step(st);
+        memcpy(m->col[j], st, sizeof(st));
+    }
+}
+
+static void xorshift32_matrix(gf2mat *m)
+{
+    memset(m, 0, sizeof(*m));
+    m->nbits = 32;
+    for (int j = 0; j < 32; ++j) {
+        uint32_t y = 1u << j;
+        oracle_xorshift32_step(&y);
+        m->col[j][0] = y;
+    }
+}
+
+void oracle_xor128_jump(uint32_t st[4], uint64_t k)
+{
+    gf2mat m, mk;
+    xor128_matrix(&m);
+    gf2_pow(&m, k, &mk);
+    gf2_apply(&mk, st, st);
+}
+
+void oracle_xorshift32_jump(uint32_t *y, uint64_t k)
+{
+    gf2mat m, mk;
+    xorshift32_matrix(&m);
+    gf2_pow(&m, k, &mk);
+    uint32_t v[4] = {*y, 0, 0, 0};
+    gf2_apply(&mk, v, v);
+    *y = v[0];
+}
+
+/* Eq. 7's map z -> A z + C (mod 2^32) applied k times.  Two affine maps
+ * compose as (A1, C1) after (A2, C2) = (A1 A2, A1 C2 + C1). */
+void oracle_lcg_jump(uint32_t *z, uint64_t k)
+{
+    uint64_t m = (uint64_t)1 << 32;
+    uint64_t RA = 1, RC = 0;              /* result: the identity map */
+    uint64_t BA = 69069, BC = 1234567;    /* base: one step */
+    while (k) {
+        if (k & 1) {
+            RC = (BA * RC + BC) % m;      /* base after result */
+            RA = (BA * RA) % m;
+        }
+        BC = (BA * BC + BC) % m;          /* base after base */
+        BA = (BA * BA) % m;
+        k >>= 1;
+    }
+    *z = (uint32_t)((RA * (uint64_t)(*z) + RC) % m);
+}
+
+void oracle_jump(int kind, uint32_t a, uint32_t st[4], uint64_t k)
+{
+    if (kind == 0) {
+        oracle_mwc_jump(a, &st[0], &st[1], k, 32);
+    } else if (kind == 1) {
+        oracle_xor128_jump(st, k);
+    } else {
+        oracle_mwc_jump(a, &st[0], &st[1], k, 32);
+        oracle_xorshift32_jump(&st[2], k);
+        oracle_lcg_jump(&st[3], k);
+    }
 }

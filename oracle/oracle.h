@@ -62,6 +62,23 @@ void oracle_generate(int kind, uint64_t n_streams, const uint32_t *a,
                      uint32_t *state, uint64_t n_per_stream, int fmt,
                      void *out);
 
+/* consumers with no output array (Sec. "Performance evaluation": numbers
+ * used inline, only the final state stored) */
+uint64_t oracle_sum_u32(const uint32_t *u, uint64_t n);
+uint64_t oracle_sum_u24(const uint32_t *u, uint64_t n);
+uint64_t oracle_disc_count(const uint32_t *u, uint64_t n);
+int oracle_reduce(int kind, uint64_t n_streams, const uint32_t *a,
+                  uint32_t *state, uint64_t n_per_stream, int op,
+                  uint64_t *out);
+
+/* jump-ahead by k steps (Sec. "Parallelizing RNGs", sequence splitting) */
+void oracle_mwc_jump(uint32_t a, uint32_t *x, uint32_t *c, uint64_t k,
+                     int log2b);
+void oracle_xor128_jump(uint32_t st[4], uint64_t k);
+void oracle_xorshift32_jump(uint32_t *y, uint64_t k);
+void oracle_lcg_jump(uint32_t *z, uint64_t k);
+void oracle_jump(int kind, uint32_t a, uint32_t st[4], uint64_t k);
+
 /* brute-force periods (pins) */
 uint64_t oracle_mwc_period(uint32_t a, uint32_t x0, uint32_t c0, int log2b,
                            uint64_t limit);

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_consumers_jump as cj
 import test_oracle_pins as pins
 
 SRC = (oracle.HERE / "oracle.c").read_text()
@@ -47,6 +48,27 @@ MUTANTS = [
      "return 1 && ", pins.check_mwc16_multiplier_count),
     ("trial division misses 3", "for (int i = 3; i < 1024; i += 2)",
      "for (int i = 5; i < 1024; i += 2)", pins.check_mwc16_multipliers_brute_force),
+    ("sum skips the first output", "for (uint64_t j = 0; j < n; ++j)\n        s += (uint64_t)u[j];",
+     "for (uint64_t j = 1; j < n; ++j)\n        s += (uint64_t)u[j];", cj.check_sum_closed_forms),
+    ("24-bit sum keeps 25 bits", "s += (uint64_t)(u[j] >> 8);", "s += (uint64_t)(u[j] >> 7);",
+     cj.check_sum_closed_forms),
+    ("disc count uses 23 bits", "uint64_t X = u[2 * k] >> 8;", "uint64_t X = u[2 * k] >> 9;",
+     cj.check_disc_lattice_count),
+    ("disc count pairs overlap",
+     "uint64_t X = u[2 * k] >> 8;\n        uint64_t Y = u[2 * k + 1] >> 8;",
+     "uint64_t X = u[k] >> 8;\n        uint64_t Y = u[k + 1] >> 8;", cj.check_disc_lattice_count),
+    ("disc radius squared is 2^47", "X * X + Y * Y < ((uint64_t)1 << 48)",
+     "X * X + Y * Y < ((uint64_t)1 << 47)", cj.check_disc_estimates_pi),
+    ("MWC jump: x and carry swapped", "*x = (uint32_t)(t / a);\n    *c = (uint32_t)(t % a);",
+     "*c = (uint32_t)(t / a);\n    *x = (uint32_t)(t % a);", cj.check_jump_equals_stepping),
+    ("MWC jump multiplies by b^k", "oracle_powmod_u64(a, k, p)",
+     "oracle_powmod_u64((uint64_t)1 << log2b, k, p)", cj.check_mwc_jump_lehmer),
+    ("GF(2) apply drops the top word", "for (int w = 0; w < 4; ++w)\n                r[w] ^= m->col[j][w];",
+     "for (int w = 0; w < 3; ++w)\n                r[w] ^= m->col[j][w];", cj.check_jump_equals_stepping),
+    ("GF(2) power uses the wrong bit", "if (k & 1)\n            gf2_mul(&result, &base, &result);",
+     "if (k & 2)\n            gf2_mul(&result, &base, &result);", cj.check_jump_periods),
+    ("LCG jump drops the increment", "RC = (BA * RC + BC) % m;", "RC = (BA * RC) % m;",
+     cj.check_jump_equals_stepping),
 ]
 
 
