@@ -123,6 +123,14 @@ int rng_state_words(rng_handle h);
  * registers variant, KISS) and the uniform variant of Sec. "Performance
  * evaluation". */
 int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int fmt);
+/* Few streams with long sequences: when n_streams is too small to fill the
+ * device and rows are 32-byte aligned, rng_generate cuts each stream's
+ * outputs into segments of 2^l rows (l chosen per kind; gbrng_set_split),
+ * starts every segment from the state jumped ahead to it (rng_jump) and
+ * runs the segments side by side; the final state goes through a scratch
+ * buffer allocated with the handle on first use (RNG_ERR_OOM if that
+ * fails).  The outputs and the state are those of the plain sequence
+ * (sequence splitting, Sec. "Parallelizing RNGs"). */
 
 /* Advances only streams [s_begin, s_end) (0 <= s_begin < s_end <= n_streams)
  * n_per_stream times; the other streams keep their state.  Output j of
@@ -160,6 +168,61 @@ int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host_out,
  * the sequence can continue (Sec. "Performance evaluation"). */
 int rng_get_state(rng_handle h, void *host_buf, size_t bytes);
 int rng_set_state(rng_handle h, const void *host_buf, size_t bytes);
+
+/* Inline consumers (op) of rng_generate_reduce. */
+enum rng_reduce_op {
+    RNG_SUM_U32 = 0, /* sum of the outputs, mod 2^64                          */
+    RNG_SUM_U24 = 1, /* sum of u >> 8: exactly 2^24 x the sum of the uniforms  */
+    RNG_DISC = 2     /* outputs taken in consecutive pairs (u0, u1) as points
+                        (x, y) of their uniforms: the number of points with
+                        x^2 + y^2 < 1, tested exactly as
+                        (u0>>8)^2 + (u1>>8)^2 < 2^48; an unpaired last output
+                        is drawn and ignored.  4 x count / pairs estimates pi */
+};
+
+/* Advances every stream n_per_stream times, exactly as rng_generate does
+ * (same state afterwards), but writes no outputs: each output is consumed
+ * where it is made, and out[s] receives the consumer `op` applied to
+ * stream s's outputs of this call.  `out` is a DEVICE pointer, caller-owned,
+ * n_streams uint64 values, 8-byte aligned.  Asynchronous on the handle's
+ * stream.  Errors: RNG_ERR_ARG (NULL handle or out, bad op, misaligned
+ * out), RNG_ERR_OOM (the split scratch, below), RNG_ERR_CUDA.
+ * Few streams with long sequences are split like rng_generate's (each
+ * stream's outputs cut into segments that start from jumped states; the
+ * segment results are added, which is exact in integers).
+ * Paper: the generators timed without writing the numbers back, only the
+ * final state (Sec. "Performance evaluation"; Tables I-III). */
+int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, void *out);
+
+/* Advances every stream by k steps without computing the outputs in
+ * between, in O(log k) work per stream: MWC by modular exponentiation
+ * (with p = a 2^32 - 1 and t = a x + c, one step maps t to a t mod p), the
+ * xorshift parts by powers of their GF(2) matrices (tables of M^(2^m) built
+ * once per device on first use; synchronises then), the LCG by composing
+ * its affine map.  The state afterwards equals k single steps.
+ * Asynchronous on the handle's stream.  Errors: RNG_ERR_ARG, RNG_ERR_OOM,
+ * RNG_ERR_CUDA.
+ * Paper: sequence splitting needs the i-th number without the ones before
+ * it (Sec. "Parallelizing RNGs"). */
+int rng_jump(rng_handle h, uint64_t k);
+
+/* Where a handle's state lives, for kernels that step the streams
+ * themselves (include/gbrng_device.cuh, Engine<KIND>). */
+typedef struct rng_device_view {
+    int kind;            /* rng_kind                                         */
+    int device;          /* CUDA device of the handle                        */
+    int state_words;     /* 2 (MWC32) or 4                                   */
+    uint64_t n_streams;
+    void *state;         /* DEVICE uint32: word w of stream s at
+                            state[w * n_streams + s]; owned by the handle    */
+    const void *mult;    /* DEVICE uint32 multiplier of stream s at mult[s]
+                            (MWC32, KISS); NULL for xor128                   */
+} rng_device_view;
+
+/* Fills *view.  The pointers stay valid until rng_destroy.  A kernel that
+ * reads or writes the state must be ordered with the handle's own work
+ * (enqueue it on the handle's stream).  Errors: RNG_ERR_ARG. */
+int rng_get_device_view(rng_handle h, rng_device_view *view);
 
 /* Writes the first k stream multipliers (the MWC32/KISS table: a < 2^32,
  * largest first, a*2^32 - 1 a safe prime) to `dev_out` (DEVICE pointer,

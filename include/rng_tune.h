@@ -23,6 +23,12 @@ extern "C" {
 int gbrng_set_launch(int kind, int fmt, int v, int block, int hint);
 int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
 
+/* Sequence splitting of few-stream calls (rng_generate, rng_generate_reduce):
+ * `log2_rows` is log2 of the fewest rows a segment may have for `kind`
+ * (1..30); 0 turns splitting off for the kind.  Outputs never change. */
+int gbrng_set_split(int kind, int log2_rows);
+int gbrng_get_split(int kind, int *log2_rows);
+
 /* Write-only bandwidth probe: fills `bytes` (a multiple of 16) of the DEVICE
  * buffer `dst` with 16-byte stores from a grid of `blocks` x `threads`
  * (grid-stride), on `cuda_stream`, `reps` times back to back.  hint as

@@ -23,7 +23,7 @@ LIBDIR = PKG / "_lib"
 LIB = LIBDIR / "libgbrng.so"
 
 SOURCES = ["api.cu", "multipliers.cu", "seed.cu", "generate.cu", "batch.cu",
-           "probe.cu", "serve.cu"]
+           "probe.cu", "serve.cu", "jump.cu", "reduce.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-Xcompiler", "-Wall", "-I", str(INCLUDE), "-I", str(CSRC)]
@@ -38,7 +38,7 @@ def nvcc() -> str:
 
 def _deps() -> list[Path]:
     return ([CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) +
-            list(INCLUDE.glob("*.h")) + [Path(__file__)])
+            list(INCLUDE.glob("*.h")) + list(INCLUDE.glob("*.cuh")) + [Path(__file__)])
 
 
 def stale() -> bool:

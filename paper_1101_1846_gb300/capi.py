@@ -18,6 +18,8 @@ RNG_ERR_TIMEOUT, RNG_ERR_BUSY, RNG_ERR_NODEV = -4, -5, -6
 RNG_MAX_STREAMS_MWC = 1 << 22
 RNG_MAX_STREAMS_XOR = 1 << 30
 
+RNG_SUM_U32, RNG_SUM_U24, RNG_DISC = 0, 1, 2
+
 KINDS = {"mwc": RNG_MWC32, "xor128": RNG_XOR128, "kiss": RNG_KISS}
 FMTS = {"u32": RNG_U32, "f32": RNG_F32}
 
@@ -27,6 +29,12 @@ class rng_batch_item(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("fmt", ctypes.c_int),
                 ("s_begin", ctypes.c_uint64), ("s_end", ctypes.c_uint64),
                 ("ld", ctypes.c_uint64)]
+
+
+class rng_device_view(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("device", ctypes.c_int),
+                ("state_words", ctypes.c_int), ("n_streams", ctypes.c_uint64),
+                ("state", ctypes.c_void_p), ("mult", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/*.h
@@ -46,6 +54,10 @@ SIGNATURES = {
     "rng_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "rng_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "rng_multipliers": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p]),
+    "rng_generate_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                           ctypes.c_void_p]),
+    "rng_jump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rng_get_device_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rng_device_view)]),
     "rng_plan_create": (ctypes.c_void_p, [ctypes.POINTER(rng_batch_item), ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int]),
     "rng_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -89,6 +101,8 @@ SIGNATURES = {
     "gbrng_set_launch": (ctypes.c_int, [ctypes.c_int] * 5),
     "gbrng_get_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] +
                          [ctypes.POINTER(ctypes.c_int)] * 3),
+    "gbrng_set_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "gbrng_get_split": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbrng_probe_write": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_void_p]),

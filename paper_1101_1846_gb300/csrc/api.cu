@@ -55,6 +55,7 @@ void free_gen(Gen *g)
         return;
     cudaFree(g->d_state);
     cudaFree(g->d_a);
+    cudaFree(g->d_split);
     for (int i = 0; i < 2; ++i) {
         cudaFree(g->d_stage[i]);
         if (g->stage_ev[i])
@@ -120,6 +121,15 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
         if (!st)
             st = cuda_status(cudaMemcpy(g->d_a, table, n_streams * 4, cudaMemcpyDeviceToDevice));
     }
+    // scratch for the final state of split calls (few streams only)
+    if (!st && n_streams <= kSplitMaxStreams &&
+        cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess)
+        st = set_error(RNG_ERR_OOM);
+    // jump tables of the xorshift and LCG parts, built here so that no later
+    // call (which may be captured in a CUDA graph) has to build them
+    JumpTables tables;
+    if (!st && kind != RNG_MWC32)
+        st = jump_tables(&tables);
     if (!st)
         st = launch_seed(g, nullptr);
     if (!st)
@@ -176,7 +186,7 @@ extern "C" int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int 
     DeviceGuard dg(g->device);
     if (!dg.ok)
         return set_error(RNG_ERR_CUDA);
-    GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, n_per_stream, out, g->n};
+    GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, n_per_stream, out, g->n, g->d_split};
     return launch_generate(g->kind, fmt, p, g->stream);
 }
 
@@ -195,7 +205,7 @@ extern "C" int rng_generate_range(rng_handle h, uint64_t s_begin, uint64_t s_end
     DeviceGuard dg(g->device);
     if (!dg.ok)
         return set_error(RNG_ERR_CUDA);
-    GenLaunch p{g->d_state, g->d_a, g->n, s_begin, s_end, n_per_stream, out, ld};
+    GenLaunch p{g->d_state, g->d_a, g->n, s_begin, s_end, n_per_stream, out, ld, g->d_split};
     return launch_generate(g->kind, fmt, p, g->stream);
 }
 
@@ -250,7 +260,7 @@ extern "C" int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host
         // buffer b is free once its previous copy (chunk - 2) has finished
         if (chunk >= 2)
             st = cuda_status(cudaStreamWaitEvent(g->stream, g->stage_ev[b], 0));
-        GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, m, g->d_stage[b], g->n};
+        GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, m, g->d_stage[b], g->n, g->d_split};
         if (!st)
             st = launch_generate(g->kind, fmt, p, g->stream);
         if (!st)
@@ -274,6 +284,26 @@ extern "C" int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host
     if (!st && e2 != cudaSuccess)
         st = cuda_status(e2);
     return st;
+}
+
+extern "C" int rng_jump(rng_handle h, uint64_t k)
+{
+    Gen *g = reinterpret_cast<Gen *>(h);
+    if (!g)
+        return set_error(RNG_ERR_ARG);
+    DeviceGuard dg(g->device);
+    if (!dg.ok)
+        return set_error(RNG_ERR_CUDA);
+    return launch_jump(g, k, g->stream);
+}
+
+extern "C" int rng_get_device_view(rng_handle h, rng_device_view *view)
+{
+    Gen *g = reinterpret_cast<Gen *>(h);
+    if (!g || !view)
+        return set_error(RNG_ERR_ARG);
+    *view = rng_device_view{g->kind, g->device, g->words, g->n, g->d_state, g->d_a};
+    return RNG_OK;
 }
 
 extern "C" int rng_get_state(rng_handle h, void *host_buf, size_t bytes)

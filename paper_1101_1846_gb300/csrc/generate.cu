@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include "gen_body.cuh"
+#include "jump.cuh"
 #include "rng_tune.h"
 
 namespace gbrng {
@@ -82,6 +83,63 @@ gen_shift(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
                                 (uint32_t)(left < per_cta ? left : per_cta));
 }
 
+// Sequence splitting (Sec. "Parallelizing RNGs") for calls with too few
+// streams to fill the device: segment y of the grid produces rows
+// [y*rows, min(steps, (y+1)*rows)) of every stream, starting from the state
+// jumped ahead by y*rows steps.  One group of four streams per thread, rows
+// 32-byte aligned (as gen_vec).  The state is only read; the last segment
+// writes the final state to `final_state` (same layout), which the host
+// copies back after the kernel, so no segment can read a state that another
+// has already advanced.
+template <int KIND, int FMT, int HINT>
+__global__ void __launch_bounds__(256)
+gen_split(const uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
+          uint32_t steps, uint32_t rows, uint32_t *__restrict__ out, uint64_t ld,
+          uint64_t s_begin, uint64_t count, uint32_t *__restrict__ final_state, JumpTables T)
+{
+    const uint64_t c_first = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c_first >= count)
+        return;
+    constexpr int W = Words<KIND>::W;
+    const uint64_t s0 = s_begin + c_first;
+    const uint32_t first = blockIdx.y * rows;
+    const uint32_t mine = min(rows, steps - first);
+    uint32_t w[4][4] = {};
+    uint32_t a[4] = {};
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+        load4(state + k * n + s0, w[k]);
+    if constexpr (KIND != RNG_XOR128)
+        load4(mult + s0, a);
+    jump_streams<KIND, 4>(w, a, first, T);
+    uint32_t *row = out + (uint64_t)first * ld + c_first;
+#pragma unroll 4
+    for (uint32_t j = 0; j < mine; ++j) {
+        const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+        const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+        const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+        const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+        store16<HINT>(row, o0, o1, o2, o3);
+        row += ld;
+    }
+    if (blockIdx.y == gridDim.y - 1) {
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            save4(final_state + k * n + s0, w[k]);
+    }
+}
+
+using SplitFn = void (*)(const uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t,
+                         uint32_t *, uint64_t, uint64_t, uint64_t, uint32_t *, JumpTables);
+
+template <int KIND>
+SplitFn pick_split(int fmt, int hint)
+{
+    if (fmt == RNG_F32)
+        return hint ? gen_split<KIND, RNG_F32, 1> : gen_split<KIND, RNG_F32, 0>;
+    return hint ? gen_split<KIND, RNG_U32, 1> : gen_split<KIND, RNG_U32, 0>;
+}
+
 using VecFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t *, uint64_t,
                        uint64_t, uint64_t);
 using ShiftFn = VecFn;
@@ -135,6 +193,13 @@ Shape g_shape[3][2] = {
 };
 
 constexpr int kSMs = 152;
+// Fewest rows of a split segment, as log2, per kind (0: never split).  The
+// jump that starts a segment costs about as much as this many rows: MWC a
+// few dozen Montgomery products, KISS those plus 32-column GF(2) products,
+// xor128 128-column products.
+int g_split_log2[3] = {6, 7, 10};
+// Threads that fill the device (CTAs of 256 at full occupancy).
+constexpr uint64_t kFillThreads = (uint64_t)kSMs * 1024;
 // CTA size of the kernels with row barriers: large CTAs leave fewer CTA
 // boundaries, where neighbouring CTAs that drift apart split sectors.
 constexpr int kSyncBlock = 512;
@@ -149,6 +214,27 @@ int fit_threads(int threads, uint64_t units)
 }
 
 }  // namespace
+
+bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per_thread,
+                uint64_t *rows, uint64_t *segments)
+{
+    const int l0 = g_split_log2[kind];
+    if (l0 == 0 || streams == 0 || streams > kSplitMaxStreams || steps > (1ull << 31))
+        return false;
+    const uint64_t threads = (streams + streams_per_thread - 1) / streams_per_thread;
+    if (2 * threads > kFillThreads)
+        return false;  // enough streams to fill the device already
+    const uint64_t want = std::min<uint64_t>(kFillThreads / threads, 65535);
+    uint64_t L = 1ull << l0;
+    while (L < steps && (steps + L - 1) / L > want)
+        L <<= 1;
+    const uint64_t S = (steps + L - 1) / L;
+    if (S < 2)
+        return false;
+    *rows = L;
+    *segments = S;
+    return true;
+}
 
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
 {
@@ -174,6 +260,28 @@ int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
     const bool sectors = aligned && (p.ld % 8 == 0) && ((uintptr_t)p.out % 32 == 0);
     const uint64_t main = count & ~(uint64_t)3;
     uint32_t *out = static_cast<uint32_t *>(p.out);
+    uint64_t L = 0, S = 0;
+    if (p.split && sectors && split_plan(kind, count, p.steps, 4, &L, &S)) {
+        JumpTables T{};
+        if (kind != RNG_MWC32) {
+            int e = jump_tables(&T);
+            if (e)
+                return e;
+        }
+        SplitFn fn = kind == RNG_MWC32    ? pick_split<RNG_MWC32>(fmt, sh.hint)
+                     : kind == RNG_XOR128 ? pick_split<RNG_XOR128>(fmt, sh.hint)
+                                          : pick_split<RNG_KISS>(fmt, sh.hint);
+        const dim3 grid((unsigned)((count / 4 + 255) / 256), (unsigned)S);
+        fn<<<grid, 256, 0, st>>>(p.state, p.a, p.n, (uint32_t)p.steps, (uint32_t)L, out, p.ld,
+                                 p.s_begin, count, p.split, T);
+        int e = cuda_status(cudaGetLastError());
+        if (e)
+            return e;
+        const int W = words_of(kind);
+        return cuda_status(cudaMemcpy2DAsync(p.state + p.s_begin, p.n * 4, p.split + p.s_begin,
+                                             p.n * 4, count * 4, W, cudaMemcpyDeviceToDevice,
+                                             st));
+    }
     // Calls longer than 2^31 steps are cut into pieces (the kernels count
     // steps in 32 bits); the state carries from piece to piece.
     for (uint64_t done = 0; done < p.steps;) {
@@ -225,6 +333,24 @@ extern "C" int gbrng_set_launch(int kind, int fmt, int v, int block, int hint)
         block > 512 || (block & (block - 1)) || hint < 0 || hint > 1)
         return set_error(RNG_ERR_ARG);
     g_shape[kind][fmt] = Shape{v, block, hint};
+    return RNG_OK;
+}
+
+extern "C" int gbrng_set_split(int kind, int log2_rows)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind > 2 || log2_rows < 0 || log2_rows > 30)
+        return set_error(RNG_ERR_ARG);
+    g_split_log2[kind] = log2_rows;
+    return RNG_OK;
+}
+
+extern "C" int gbrng_get_split(int kind, int *log2_rows)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind > 2 || !log2_rows)
+        return set_error(RNG_ERR_ARG);
+    *log2_rows = g_split_log2[kind];
     return RNG_OK;
 }
 

@@ -1,0 +1,159 @@
+// Jump-ahead tables and rng_jump (sequence splitting, Sec. "Parallelizing
+// RNGs").  The tables hold, for m = 0..63, the GF(2) matrix of 2^m xor128
+// steps (128 columns of 4 words), of 2^m xorshift32 steps (32 columns) and
+// the affine map (A, C) of 2^m LCG steps.  One CTA builds them on the
+// device by repeated squaring, once per device and process.
+#include <mutex>
+
+#include "jump.cuh"
+
+namespace gbrng {
+namespace {
+
+constexpr int kLevels = 64;
+constexpr int kMaxDevices = 64;
+
+struct DeviceTables {
+    void *mem = nullptr;
+    JumpTables t{};
+};
+DeviceTables g_tables[kMaxDevices];
+std::mutex g_mutex;
+
+// Column j of level m is level m-1 applied to its own column j.
+__global__ void __launch_bounds__(128) build_tables(uint4 *t128, uint32_t *t32, uint2 *tl)
+{
+    __shared__ uint4 cur[128];
+    __shared__ uint32_t cur32[32];
+    const int j = threadIdx.x;
+    {
+        uint32_t s[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            s[q] = (j >> 5) == q ? 1u << (j & 31) : 0u;
+        xor128_step(s[0], s[1], s[2], s[3]);
+        cur[j] = make_uint4(s[0], s[1], s[2], s[3]);
+        t128[j] = cur[j];
+        if (j < 32) {
+            uint32_t y = 1u << j;
+            xorshift32_step(y);
+            cur32[j] = y;
+            t32[j] = y;
+        }
+    }
+    for (int m = 1; m < kLevels; ++m) {
+        __syncthreads();
+        const uint4 v = cur[j];
+        const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+        uint4 r = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            for (int b = 0; b < 32; ++b) {
+                if ((vw[q] >> b) & 1u) {
+                    const uint4 c = cur[32 * q + b];
+                    r.x ^= c.x;
+                    r.y ^= c.y;
+                    r.z ^= c.z;
+                    r.w ^= c.w;
+                }
+            }
+        }
+        uint32_t r32 = 0;
+        if (j < 32) {
+            const uint32_t y = cur32[j];
+            for (int b = 0; b < 32; ++b)
+                if ((y >> b) & 1u)
+                    r32 ^= cur32[b];
+        }
+        __syncthreads();
+        cur[j] = r;
+        t128[m * 128 + j] = r;
+        if (j < 32) {
+            cur32[j] = r32;
+            t32[m * 32 + j] = r32;
+        }
+    }
+    if (j == 0) {
+        uint32_t A = 69069u, C = 1234567u;  // one step of Eq. 7
+        for (int m = 0; m < kLevels; ++m) {
+            tl[m] = make_uint2(A, C);
+            C = A * C + C;  // the map after itself
+            A = A * A;
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) jump_kernel(rng_device_view v, uint64_t k, JumpTables T)
+{
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= v.n_streams)
+        return;
+    Engine<KIND> e;
+    e.load(v, s);
+    jump_engine<KIND>(e, k, T);
+    e.store(v, s);
+}
+
+}  // namespace
+
+int jump_tables(JumpTables *out)
+{
+    int dev = 0;
+    int st = cuda_status(cudaGetDevice(&dev));
+    if (st)
+        return st;
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(RNG_ERR_NODEV);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DeviceTables &d = g_tables[dev];
+    if (!d.mem) {
+        const size_t b128 = sizeof(uint4) * 128 * kLevels;
+        const size_t b32 = sizeof(uint32_t) * 32 * kLevels;
+        const size_t bl = sizeof(uint2) * kLevels;
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, b128 + b32 + bl) != cudaSuccess)
+            return set_error(RNG_ERR_OOM);
+        char *base = static_cast<char *>(mem);
+        uint4 *t128 = reinterpret_cast<uint4 *>(base);
+        uint32_t *t32 = reinterpret_cast<uint32_t *>(base + b128);
+        uint2 *tl = reinterpret_cast<uint2 *>(base + b128 + b32);
+        build_tables<<<1, 128>>>(t128, t32, tl);
+        st = cuda_status(cudaGetLastError());
+        if (!st)
+            st = cuda_status(cudaStreamSynchronize(0));
+        if (st) {
+            cudaFree(mem);
+            return st;
+        }
+        d.mem = mem;
+        d.t = JumpTables{t128, t32, tl};
+    }
+    *out = d.t;
+    return RNG_OK;
+}
+
+int launch_jump(Gen *g, uint64_t k, cudaStream_t stream)
+{
+    if (k == 0)
+        return RNG_OK;
+    JumpTables T{};
+    if (g->kind != RNG_MWC32) {
+        int st = jump_tables(&T);
+        if (st)
+            return st;
+    }
+    rng_device_view v{g->kind, g->device, g->words, g->n, g->d_state, g->d_a};
+    const uint64_t blocks = (g->n + 255) / 256;
+    if (blocks > 0x7FFFFFFFull)
+        return set_error(RNG_ERR_ARG);
+    if (g->kind == RNG_MWC32)
+        jump_kernel<RNG_MWC32><<<(unsigned)blocks, 256, 0, stream>>>(v, k, T);
+    else if (g->kind == RNG_XOR128)
+        jump_kernel<RNG_XOR128><<<(unsigned)blocks, 256, 0, stream>>>(v, k, T);
+    else
+        jump_kernel<RNG_KISS><<<(unsigned)blocks, 256, 0, stream>>>(v, k, T);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace gbrng

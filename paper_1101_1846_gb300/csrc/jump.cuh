@@ -1,0 +1,158 @@
+// Jump-ahead on the device: the state of a stream k steps later without
+// the steps in between (sequence splitting, Sec. "Parallelizing RNGs").
+//
+//   MWC     With p = a 2^32 - 1 and t = a x + c (0 < t < p), one step maps t
+//           to a t mod p (a = 2^-32 mod p; the step is Lehmer's generator
+//           in disguise), so k steps multiply t by a^k mod p.  In Montgomery
+//           form with R = 2^64, a R = 2^32 (mod p) since a 2^32 = p + 1, and
+//           -p^-1 = 1 + a 2^32 (mod 2^64) since p (1 + a 2^32) = a^2 2^64 - 1:
+//           no division or inversion is needed to set up the powering.
+//           Multiplying a residue X = h 2^32 + l by a is a l + h (< p): one
+//           MWC step applied to X.
+//   xor128, xorshift32
+//           GF(2)-linear: k steps apply M^k, the product of the tables'
+//           M^(2^m) over the set bits m of k (powers of one matrix commute).
+//   LCG     affine: the composed maps (A_m, C_m) of 2^m steps.
+#pragma once
+
+#include "gbrng.cuh"
+#include "modarith.cuh"
+
+namespace gbrng {
+
+__device__ __forceinline__ uint64_t mwc_mul_a(uint64_t X, uint32_t a)
+{
+    return (uint64_t)a * (uint32_t)X + (X >> 32);
+}
+
+__device__ __forceinline__ void mwc_jump(uint32_t a, uint32_t &x, uint32_t &c, uint64_t k)
+{
+    if (k == 0)
+        return;
+    const uint64_t p = ((uint64_t)a << 32) - 1;
+    const uint64_t ninv = ((uint64_t)a << 32) + 1;
+    uint64_t A = (uint64_t)1 << 32;  // a^1 in Montgomery form: the top bit of k
+    for (int bit = 62 - __clzll((long long)k); bit >= 0; --bit) {
+        A = mont_mul(A, A, p, ninv);
+        if ((k >> bit) & 1)
+            A = mwc_mul_a(A, a);
+    }
+    const uint64_t t = mont_mul(A, (uint64_t)a * x + c, p, ninv);  // a^k t mod p
+    x = (uint32_t)(t / a);
+    c = (uint32_t)(t - (uint64_t)x * a);
+}
+
+// v <- M v for a 128 x 128 GF(2) matrix given by columns (word w of column j
+// in col[j]); the four streams of a group share every column load.
+template <int G>
+__device__ __forceinline__ void gf2_apply128(const uint4 *__restrict__ col,
+                                             uint32_t (&w)[4][4])
+{
+    uint32_t r[4][G];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            r[q][i] = 0;
+#pragma unroll
+    for (int word = 0; word < 4; ++word) {
+#pragma unroll 4
+        for (int b = 0; b < 32; ++b) {
+            const uint4 m = __ldg(col + 32 * word + b);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                const uint32_t mask = 0u - ((w[word][i] >> b) & 1u);
+                r[0][i] ^= m.x & mask;
+                r[1][i] ^= m.y & mask;
+                r[2][i] ^= m.z & mask;
+                r[3][i] ^= m.w & mask;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            w[q][i] = r[q][i];
+}
+
+__device__ __forceinline__ uint32_t gf2_apply32(const uint32_t *__restrict__ col, uint32_t y)
+{
+    uint32_t r = 0;
+#pragma unroll 8
+    for (int b = 0; b < 32; ++b)
+        r ^= __ldg(col + b) & (0u - ((y >> b) & 1u));
+    return r;
+}
+
+// Jumps G streams held as w[word][i] (the vector bodies' layout; G = 1 for
+// a single stream) with multipliers a[i] by k steps.
+template <int KIND, int G>
+__device__ __forceinline__ void jump_streams(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+                                             uint64_t k, const JumpTables &T)
+{
+    if (k == 0)
+        return;
+    if constexpr (KIND == RNG_MWC32) {
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            mwc_jump(a[i], w[0][i], w[1][i], k);
+    } else if constexpr (KIND == RNG_XOR128) {
+        for (uint64_t r = k; r; r &= r - 1)
+            gf2_apply128<G>(T.xor128 + 128 * (__ffsll((long long)r) - 1), w);
+    } else {
+#pragma unroll
+        for (int i = 0; i < G; ++i)
+            mwc_jump(a[i], w[0][i], w[1][i], k);
+        for (uint64_t r = k; r; r &= r - 1) {
+            const int m = __ffsll((long long)r) - 1;
+            const uint2 lc = __ldg(T.lcg + m);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                w[2][i] = gf2_apply32(T.xs32 + 32 * m, w[2][i]);
+                w[3][i] = lc.x * w[3][i] + lc.y;
+            }
+        }
+    }
+}
+
+// The same for one stream in an Engine.
+template <int KIND>
+__device__ __forceinline__ void jump_engine(Engine<KIND> &e, uint64_t k, const JumpTables &T)
+{
+    uint32_t w[4][4] = {};
+    uint32_t a[4] = {};
+    if constexpr (KIND == RNG_MWC32) {
+        w[0][0] = e.x;
+        w[1][0] = e.c;
+        a[0] = e.a;
+    } else if constexpr (KIND == RNG_XOR128) {
+        w[0][0] = e.s0;
+        w[1][0] = e.s1;
+        w[2][0] = e.s2;
+        w[3][0] = e.s3;
+    } else {
+        w[0][0] = e.x;
+        w[1][0] = e.c;
+        w[2][0] = e.y;
+        w[3][0] = e.z;
+        a[0] = e.a;
+    }
+    jump_streams<KIND, 1>(w, a, k, T);
+    if constexpr (KIND == RNG_MWC32) {
+        e.x = w[0][0];
+        e.c = w[1][0];
+    } else if constexpr (KIND == RNG_XOR128) {
+        e.s0 = w[0][0];
+        e.s1 = w[1][0];
+        e.s2 = w[2][0];
+        e.s3 = w[3][0];
+    } else {
+        e.x = w[0][0];
+        e.c = w[1][0];
+        e.y = w[2][0];
+        e.z = w[3][0];
+    }
+}
+
+}  // namespace gbrng

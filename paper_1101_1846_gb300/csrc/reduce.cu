@@ -1,0 +1,133 @@
+// Inline consumers (rng_generate_reduce): every stream advances exactly as
+// in rng_generate, each output is consumed in registers where it is made,
+// and only one 64-bit result per stream and the final state are written.
+// This is the paper's second regime, generation without writing the numbers
+// back (Sec. "Performance evaluation"; Tables I-III), with the numbers
+// actually used so that no step can be optimised away.  The kernels step
+// the streams through Engine<KIND> of the public device header, the same
+// path a user kernel takes.
+//
+// One stream per thread, loaded with coalesced 4-byte accesses across the
+// warp.  Few streams with long sequences are split into segments of 2^l
+// rows (split_plan; grid y = segment) that start from jumped states; their
+// results are added into out with 64-bit atomics (exact, in any order) and
+// the last segment's state goes to the scratch and is copied back.
+#include "jump.cuh"
+
+namespace gbrng {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int OP, int KIND>
+__device__ __forceinline__ uint64_t consume(Engine<KIND> &e, uint64_t m)
+{
+    uint64_t acc = 0;
+    if constexpr (OP == RNG_SUM_U32) {
+#pragma unroll 8
+        for (uint64_t j = 0; j < m; ++j)
+            acc += e.next();
+    } else if constexpr (OP == RNG_SUM_U24) {
+#pragma unroll 8
+        for (uint64_t j = 0; j < m; ++j)
+            acc += e.next() >> 8;
+    } else {
+        // pairs (u0, u1): inside when (u0>>8)^2 + (u1>>8)^2 < 2^48
+#pragma unroll 4
+        for (uint64_t j = 1; j < m; j += 2) {
+            const uint64_t X = e.next() >> 8;
+            const uint64_t Y = e.next() >> 8;
+            acc += (X * X + Y * Y) >> 48 == 0 ? 1u : 0u;
+        }
+        if (m & 1)
+            e.next();  // the unpaired last output is drawn and ignored
+    }
+    return acc;
+}
+
+template <int KIND, int OP>
+__global__ void __launch_bounds__(kThreads)
+reduce_kernel(rng_device_view v, uint64_t steps, uint64_t rows, uint64_t *__restrict__ out,
+              uint32_t *__restrict__ final_state, JumpTables T)
+{
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= v.n_streams)
+        return;
+    Engine<KIND> e;
+    e.load(v, s);
+    if (gridDim.y == 1) {
+        out[s] = consume<OP>(e, steps);
+        e.store(v, s);
+        return;
+    }
+    const uint64_t first = (uint64_t)blockIdx.y * rows;
+    const uint64_t mine = steps - first < rows ? steps - first : rows;
+    jump_engine<KIND>(e, first, T);
+    atomicAdd(reinterpret_cast<unsigned long long *>(out + s),
+              (unsigned long long)consume<OP>(e, mine));
+    if (blockIdx.y == gridDim.y - 1) {
+        rng_device_view f = v;
+        f.state = final_state;
+        e.store(f, s);
+    }
+}
+
+using ReduceFn = void (*)(rng_device_view, uint64_t, uint64_t, uint64_t *, uint32_t *,
+                          JumpTables);
+
+template <int KIND>
+ReduceFn pick(int op)
+{
+    if (op == RNG_SUM_U32)
+        return reduce_kernel<KIND, RNG_SUM_U32>;
+    if (op == RNG_SUM_U24)
+        return reduce_kernel<KIND, RNG_SUM_U24>;
+    return reduce_kernel<KIND, RNG_DISC>;
+}
+
+}  // namespace
+}  // namespace gbrng
+
+using namespace gbrng;
+
+extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, void *out)
+{
+    Gen *g = reinterpret_cast<Gen *>(h);
+    if (!g || !out || (uintptr_t)out % 8 != 0 ||
+        (op != RNG_SUM_U32 && op != RNG_SUM_U24 && op != RNG_DISC))
+        return set_error(RNG_ERR_ARG);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != g->device && cudaSetDevice(g->device) != cudaSuccess)
+        return set_error(RNG_ERR_CUDA);
+    cudaStream_t st = g->stream;
+    uint64_t *o = static_cast<uint64_t *>(out);
+    rng_device_view v{g->kind, g->device, g->words, g->n, g->d_state, g->d_a};
+    ReduceFn fn = g->kind == RNG_MWC32    ? pick<RNG_MWC32>(op)
+                  : g->kind == RNG_XOR128 ? pick<RNG_XOR128>(op)
+                                          : pick<RNG_KISS>(op);
+    uint64_t rows = n_per_stream, segs = 1;
+    // pairs never straddle segments: split rows are powers of two >= 2
+    const bool split = g->d_split && split_plan(g->kind, g->n, n_per_stream, 1, &rows, &segs);
+    if (!split) {
+        rows = n_per_stream;
+        segs = 1;
+    }
+    JumpTables T{};
+    int status = RNG_OK;
+    if (split && g->kind != RNG_MWC32)
+        status = jump_tables(&T);
+    if (!status && split)
+        status = cuda_status(cudaMemsetAsync(o, 0, g->n * 8, st));
+    if (!status) {
+        const dim3 grid((unsigned)((g->n + kThreads - 1) / kThreads), (unsigned)segs);
+        fn<<<grid, kThreads, 0, st>>>(v, n_per_stream, rows, o, g->d_split, T);
+        status = cuda_status(cudaGetLastError());
+    }
+    if (!status && split)
+        status = cuda_status(cudaMemcpyAsync(g->d_state, g->d_split, (size_t)g->words * g->n * 4,
+                                             cudaMemcpyDeviceToDevice, st));
+    if (prev >= 0 && prev != g->device)
+        cudaSetDevice(prev);
+    return status;
+}

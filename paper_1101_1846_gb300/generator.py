@@ -105,6 +105,37 @@ class Generator:
                    "rng_generate_host")
         return out
 
+    def generate_reduce(self, n_per_stream: int, op: int | str = capi.RNG_SUM_U32,
+                        out: torch.Tensor | None = None,
+                        stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+        """Advances every stream n_per_stream times with no output array;
+        returns one 64-bit result per stream (an int64 tensor holding the
+        uint64 bits): op = RNG_SUM_U32, RNG_SUM_U24 or RNG_DISC
+        (rng_generate_reduce)."""
+        op = {"sum_u32": capi.RNG_SUM_U32, "sum_u24": capi.RNG_SUM_U24,
+              "disc": capi.RNG_DISC}.get(op, op) if isinstance(op, str) else op
+        if out is None:
+            out = torch.empty(self.n_streams, dtype=torch.int64, device=f"cuda:{self.device}")
+        assert out.is_cuda and out.is_contiguous() and out.element_size() == 8
+        assert out.numel() >= self.n_streams
+        self._bind(stream)
+        capi.check(capi.lib().rng_generate_reduce(self.h, n_per_stream, int(op),
+                                                  ctypes.c_void_p(out.data_ptr())),
+                   "rng_generate_reduce")
+        return out
+
+    def jump(self, k: int, stream: torch.cuda.Stream | None = None) -> None:
+        """Advances every stream by k steps without producing the outputs
+        in between (rng_jump)."""
+        self._bind(stream)
+        capi.check(capi.lib().rng_jump(self.h, int(k) & (2**64 - 1)), "rng_jump")
+
+    def device_view(self) -> capi.rng_device_view:
+        v = capi.rng_device_view()
+        capi.check(capi.lib().rng_get_device_view(self.h, ctypes.byref(v)),
+                   "rng_get_device_view")
+        return v
+
     def get_state(self) -> torch.Tensor:
         """State words as an int32 tensor (words, n_streams) on the host."""
         buf = torch.empty((self.words, self.n_streams), dtype=torch.int32)
