@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (batched, serving, other configs)")
-    p.add_argument("--workload", default="full", choices=["full", "batched", "serving"])
+    p.add_argument("--workload", default="full",
+                   choices=["full", "batched", "serving", "inline"])
     p.add_argument("--rate", type=float, default=20_000.0, help="serving: arrivals/s")
     p.add_argument("--duration", type=float, default=10.0, help="serving: seconds")
     p.add_argument("--verify-every", type=int, default=100, help="serving: check every k-th")
@@ -365,7 +366,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         del gens
         torch.cuda.empty_cache()
-        extras = run_extras(args)
+        extras = run_extras(args, (clock_info or {}).get("sm_mhz") or 2070.0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -651,17 +652,34 @@ def run_serving(args):
     return line
 
 
-def _plain_rate(kind, n, steps, fmt, seed, reps=3):
+L2_FLUSH_BYTES = 512 << 20  # four times the 129 MB L2
+
+
+def _flush_l2(_buf=[]):
+    """Writes a buffer larger than L2 so that the next timed call starts
+    with none of its output lines resident."""
+    import torch
+    if not _buf:
+        _buf.append(torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda"))
+    _buf[0].fill_(0)
+
+
+def _plain_rate(kind, n, steps, fmt, seed, reps=5):
+    """Median CUDA-event time of one rng_generate call (the L2 is flushed
+    before each timed call whose output is smaller than four L2s)."""
     import torch
 
     from paper_1101_1846_gb300.generator import Generator
     g = Generator(kind, n, seed)
     out = torch.empty((steps, n), dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream()
+    flush = 4 * n * steps < L2_FLUSH_BYTES
     g.generate(steps, fmt, out=out)
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
+        if flush:
+            _flush_l2()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
         g.generate(steps, fmt, out=out)
@@ -670,19 +688,114 @@ def _plain_rate(kind, n, steps, fmt, seed, reps=3):
         ts.append(a.elapsed_time(b))
     g.close()
     ms = sorted(ts)[len(ts) // 2]
+    return {"ms": ms, "gsamples_s": n * steps / (ms * 1e-3) / 1e9, "l2_flushed": flush}
+
+
+# Integer operations per sample in the paper's counting (Eq. 9's n_ops: every
+# 32-bit shift, logical op, add or multiply-add counts one): MWC32 = the
+# two halves of the 32 x 32 + 32 -> 64 multiply-add; xor128 = 3 shifts +
+# 4 xors; KISS = MWC 2 + xorshift32 6 + LCG 1 + 2 adds.  The sum consumer
+# adds 2 (a 64-bit add as add-with-carry).
+GEN_OPS = {0: 2, 1: 7, 2: 11}
+SUM_OPS = 2
+SMS, LANES_PER_SM_CLK = 152, 128  # 4 schedulers x 32 lanes issue per clock
+
+
+def alu_peak_tops(mhz: float) -> float:
+    """Issue-limited integer rate: 152 SMs x 4 schedulers x 32 lanes per
+    clock, at the given SM clock."""
+    return SMS * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+
+
+def _reduce_rate(kind, n, steps, op, seed, reps=5):
+    import torch
+
+    from paper_1101_1846_gb300.generator import Generator
+    g = Generator(kind, n, seed)
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    g.generate_reduce(steps, op, out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        g.generate_reduce(steps, op, out=out)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    g.close()
+    ms = sorted(ts)[len(ts) // 2]
     return {"ms": ms, "gsamples_s": n * steps / (ms * 1e-3) / 1e9}
 
 
-def run_extras(args):
+def _jump_ms(kind, n, k, seed, reps=5):
+    import torch
+
+    from paper_1101_1846_gb300.generator import Generator
+    g = Generator(kind, n, seed)
+    s = torch.cuda.current_stream()
+    g.jump(k)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        g.jump(k)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    g.close()
+    return sorted(ts)[len(ts) // 2]
+
+
+def run_inline(clock_mhz: float):
+    """The generators with the numbers used in registers (no output array):
+    per kind, the sum consumer and the quarter-disc count at 2^22 streams x
+    1024 outputs, with the integer-ALU roofline of the sum consumer; and
+    rng_jump over 2^22 streams."""
+    import ctypes
+
+    from paper_1101_1846_gb300 import capi
+    n, steps = 1 << 22, 1024
+    peak = alu_peak_tops(clock_mhz)
+    res = {"workload": f"2^22 streams x {steps} outputs, no output array",
+           "alu_peak_tops": peak, "alu_peak_basis": f"152 SMs x 128 lanes/clk x {clock_mhz} MHz",
+           "kinds": {}}
+    for kind in KINDS:
+        r = _reduce_rate(kind, n, steps, capi.RNG_SUM_U32, 11)
+        d = _reduce_rate(kind, n, steps, capi.RNG_DISC, 11)
+        ops = GEN_OPS[kind] + SUM_OPS
+        tops = ops * n * steps / (r["ms"] * 1e-3) / 1e12
+        res["kinds"][KNAME[kind]] = {
+            "sum_u32": r, "disc": d,
+            "roofline": {"bound": "alu", "achieved": tops, "peak": peak, "unit": "Tops/s",
+                         "frac": tops / peak, "ops_per_sample": ops},
+            "jump_2^22_streams_by_2^40+1_ms": _jump_ms(kind, n, (1 << 40) + 1, 5)}
+    # few streams: the 4096 x 4096 MWC call with and without splitting
+    v = ctypes.c_int()
+    capi.check(capi.lib().gbrng_get_split(0, ctypes.byref(v)))
+    res["mwc_u32_4096x4096_split"] = _plain_rate(0, 4096, 4096, 0, 42)
+    capi.check(capi.lib().gbrng_set_split(0, 0))
+    try:
+        res["mwc_u32_4096x4096_unsplit"] = _plain_rate(0, 4096, 4096, 0, 42)
+    finally:
+        capi.check(capi.lib().gbrng_set_split(0, v.value))
+    return res
+
+
+def run_extras(args, clock_mhz: float = 2070.0):
     """The other workloads, summarised for the same JSON line: the 2^20 x 1024
-    xor128/KISS calls, the 4096 x 4096 MWC call (few streams, latency-bound),
-    the batched 10,000-instance workload and the serving loop."""
+    xor128/KISS calls, the 4096 x 4096 MWC call (few streams: split into
+    jumped segments), the inline consumers, the batched 10,000-instance
+    workload and the serving loop."""
     extras = {"other_configs": {}}
     for kind, kn in ((1, "xor128"), (2, "kiss")):
         for fmt, fn in ((0, "u32"), (1, "f32")):
             extras["other_configs"][f"{kn}_{fn}_2^20x1024"] = _plain_rate(kind, 1 << 20, 1024,
                                                                           fmt, 7)
     extras["other_configs"]["mwc_u32_4096x4096"] = _plain_rate(0, 4096, 4096, 0, 42)
+    extras["inline"] = run_inline(clock_mhz)
     keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
             "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
             "batched_ms", "gpu_launches")
@@ -705,6 +818,8 @@ def main():
         print(json.dumps(run_batched(args)))
     elif args.workload == "serving":
         print(json.dumps(run_serving(args)))
+    elif args.workload == "inline":
+        print(json.dumps(run_inline(2070.0)))
     else:
         run_ours(args)
 

@@ -56,6 +56,8 @@ void free_gen(Gen *g)
     cudaFree(g->d_state);
     cudaFree(g->d_a);
     cudaFree(g->d_split);
+    cudaFree(g->d_cnt);
+    cudaFree(g->d_jmul);
     for (int i = 0; i < 2; ++i) {
         cudaFree(g->d_stage[i]);
         if (g->stage_ev[i])
@@ -121,10 +123,18 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
         if (!st)
             st = cuda_status(cudaMemcpy(g->d_a, table, n_streams * 4, cudaMemcpyDeviceToDevice));
     }
-    // scratch for the final state of split calls (few streams only)
-    if (!st && n_streams <= kSplitMaxStreams &&
-        cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess)
-        st = set_error(RNG_ERR_OOM);
+    // buffers of split calls (few streams only): the final-state stash, the
+    // arrival counters (zero) and the MWC jump multipliers
+    if (!st && n_streams <= kSplitMaxStreams) {
+        g->jmul_segs = split_max_segments(n_streams);
+        if (cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess ||
+            cudaMalloc(&g->d_cnt, n_streams * 4) != cudaSuccess ||
+            (kind != RNG_XOR128 &&
+             cudaMalloc(&g->d_jmul, (size_t)g->jmul_segs * n_streams * 8) != cudaSuccess))
+            st = set_error(RNG_ERR_OOM);
+        else
+            st = cuda_status(cudaMemset(g->d_cnt, 0, n_streams * 4));
+    }
     // jump tables of the xorshift and LCG parts, built here so that no later
     // call (which may be captured in a CUDA graph) has to build them
     JumpTables tables;
@@ -186,7 +196,7 @@ extern "C" int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int 
     DeviceGuard dg(g->device);
     if (!dg.ok)
         return set_error(RNG_ERR_CUDA);
-    GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, n_per_stream, out, g->n, g->d_split};
+    GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, n_per_stream, out, g->n, g};
     return launch_generate(g->kind, fmt, p, g->stream);
 }
 
@@ -205,7 +215,7 @@ extern "C" int rng_generate_range(rng_handle h, uint64_t s_begin, uint64_t s_end
     DeviceGuard dg(g->device);
     if (!dg.ok)
         return set_error(RNG_ERR_CUDA);
-    GenLaunch p{g->d_state, g->d_a, g->n, s_begin, s_end, n_per_stream, out, ld, g->d_split};
+    GenLaunch p{g->d_state, g->d_a, g->n, s_begin, s_end, n_per_stream, out, ld, g};
     return launch_generate(g->kind, fmt, p, g->stream);
 }
 
@@ -260,7 +270,7 @@ extern "C" int rng_generate_host(rng_handle h, uint64_t n_per_stream, void *host
         // buffer b is free once its previous copy (chunk - 2) has finished
         if (chunk >= 2)
             st = cuda_status(cudaStreamWaitEvent(g->stream, g->stage_ev[b], 0));
-        GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, m, g->d_stage[b], g->n, g->d_split};
+        GenLaunch p{g->d_state, g->d_a, g->n, 0, g->n, m, g->d_stage[b], g->n, g};
         if (!st)
             st = launch_generate(g->kind, fmt, p, g->stream);
         if (!st)

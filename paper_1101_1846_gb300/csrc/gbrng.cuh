@@ -24,8 +24,14 @@ struct Gen {
     uint32_t *d_state = nullptr;  // SoA: word w of stream s at d_state[w*n + s]
     uint32_t *d_a = nullptr;      // multipliers (MWC32, KISS), n entries
     cudaStream_t stream = nullptr;
-    // final state of split calls (same layout as d_state), on first use
-    uint32_t *d_split = nullptr;
+    // Split calls (few streams, long sequences; allocated at creation when
+    // n <= kSplitMaxStreams):
+    uint32_t *d_split = nullptr;  // final state stash, same layout as d_state
+    uint32_t *d_cnt = nullptr;    // arrival counters, n entries, zero between calls
+    uint64_t *d_jmul = nullptr;   // MWC jump multipliers: a^(y*jmul_rows) mod p in
+                                  // Montgomery form at d_jmul[y*n + s], y < jmul_segs
+    uint64_t jmul_rows = 0;       // rows per segment the table was built for (0: none)
+    uint32_t jmul_segs = 0;       // segments the table holds
     // staging for rng_generate_host
     void *d_stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
@@ -42,8 +48,8 @@ struct GenLaunch {
     uint64_t steps;       // outputs per stream in this call
     void *out;            // device output: element (j, s) at out[j*ld + s - s_begin]
     uint64_t ld;          // row stride in elements
-    uint32_t *split = nullptr;  // scratch for the final state of a split call
-                                // (same layout as state); nullptr: never split
+    Gen *owner = nullptr;  // handle whose split buffers a split call uses;
+                           // nullptr: never split
 };
 
 int set_error(int status);
@@ -57,11 +63,12 @@ int launch_seed(Gen *g, cudaStream_t st);
 
 // generate.cu
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st);
-// Segments of a split call: rows per segment (a power of two) and count;
-// returns false when the call should run unsplit.  `streams` are the streams
-// the call advances, `streams_per_thread` how many of them one thread takes.
+// Segments of a split call: rows per segment (a power of two) and count
+// (at most max_segments); returns false when the call should run unsplit.
+// `streams` are the streams the call advances, `streams_per_thread` how many
+// of them one thread takes.
 bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per_thread,
-                uint64_t *rows, uint64_t *segments);
+                uint64_t max_segments, uint64_t *rows, uint64_t *segments);
 
 // jump.cu: device tables of the GF(2) and affine jumps, built on first use
 // on the current device (synchronises then).
@@ -72,6 +79,11 @@ struct JumpTables {
 };
 int jump_tables(JumpTables *t);
 int launch_jump(Gen *g, uint64_t k, cudaStream_t st);
+// The handle's MWC jump multipliers for segments of `rows` rows, rebuilt on
+// `st` when `rows` differs from the table's (MWC32 and KISS handles only).
+int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **table);
+// Most segments a split call on a handle of n streams can have.
+uint32_t split_max_segments(uint64_t n);
 
 inline int words_of(int kind) { return kind == RNG_MWC32 ? 2 : 4; }
 

@@ -86,23 +86,32 @@ gen_shift(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
 // Sequence splitting (Sec. "Parallelizing RNGs") for calls with too few
 // streams to fill the device: segment y of the grid produces rows
 // [y*rows, min(steps, (y+1)*rows)) of every stream, starting from the state
-// jumped ahead by y*rows steps.  One group of four streams per thread, rows
-// 32-byte aligned (as gen_vec).  The state is only read; the last segment
-// writes the final state to `final_state` (same layout), which the host
-// copies back after the kernel, so no segment can read a state that another
-// has already advanced.
+// jumped ahead by y*rows steps (the MWC part by the handle's tabulated
+// multiplier a^(y*rows), the xorshift and LCG parts by the device tables).
+// One group of four streams per thread, rows 32-byte aligned (as gen_vec).
+//
+// Writing the final state back must wait until every segment has read the
+// start state, and no segment may wait for another.  So each thread counts
+// its arrival on the group's counter right after reading the start state;
+// the last segment also stashes its final state and counts once more.  The
+// arrival that brings the count to segments + 1 sees every read done and the
+// final state ready: it writes the state (from registers or the stash) and
+// clears the counter for the next call.
 template <int KIND, int FMT, int HINT>
 __global__ void __launch_bounds__(256)
-gen_split(const uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
+gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
           uint32_t steps, uint32_t rows, uint32_t *__restrict__ out, uint64_t ld,
-          uint64_t s_begin, uint64_t count, uint32_t *__restrict__ final_state, JumpTables T)
+          uint64_t s_begin, uint64_t count, uint32_t *__restrict__ stash,
+          uint32_t *__restrict__ counters, const uint64_t *__restrict__ jmul, JumpTables T)
 {
     const uint64_t c_first = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (c_first >= count)
         return;
     constexpr int W = Words<KIND>::W;
     const uint64_t s0 = s_begin + c_first;
-    const uint32_t first = blockIdx.y * rows;
+    const uint32_t segs = gridDim.y;
+    const uint32_t y = blockIdx.y;
+    const uint32_t first = y * rows;
     const uint32_t mine = min(rows, steps - first);
     uint32_t w[4][4] = {};
     uint32_t a[4] = {};
@@ -111,7 +120,32 @@ gen_split(const uint32_t *__restrict__ state, const uint32_t *__restrict__ mult,
         load4(state + k * n + s0, w[k]);
     if constexpr (KIND != RNG_XOR128)
         load4(mult + s0, a);
-    jump_streams<KIND, 4>(w, a, first, T);
+    __threadfence();  // the reads above are done before the arrival is counted
+    uint32_t *cnt = counters + s0 / 4;
+    bool finish = atomicAdd(cnt, 1u) == segs;
+    if (finish) {
+        // every other arrival, the stash included, came first
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(stash + k * n + s0));
+            *reinterpret_cast<uint4 *>(state + k * n + s0) = q;
+        }
+        *cnt = 0;
+    }
+    if (y > 0) {
+        if constexpr (KIND != RNG_XOR128) {
+            const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0));
+            const uint4 hi =
+                __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0 + 2));
+            const uint64_t A[4] = {(uint64_t)lo.y << 32 | lo.x, (uint64_t)lo.w << 32 | lo.z,
+                                   (uint64_t)hi.y << 32 | hi.x, (uint64_t)hi.w << 32 | hi.z};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                mwc_apply(A[i], a[i], w[0][i], w[1][i]);
+        }
+        jump_streams<KIND, 4, true>(w, a, first, T);
+    }
     uint32_t *row = out + (uint64_t)first * ld + c_first;
 #pragma unroll 4
     for (uint32_t j = 0; j < mine; ++j) {
@@ -122,15 +156,23 @@ gen_split(const uint32_t *__restrict__ state, const uint32_t *__restrict__ mult,
         store16<HINT>(row, o0, o1, o2, o3);
         row += ld;
     }
-    if (blockIdx.y == gridDim.y - 1) {
+    if (y == segs - 1) {
 #pragma unroll
         for (int k = 0; k < W; ++k)
-            save4(final_state + k * n + s0, w[k]);
+            save4(stash + k * n + s0, w[k]);
+        __threadfence();  // the stash is visible before its arrival is counted
+        if (atomicAdd(cnt, 1u) == segs) {
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                save4(state + k * n + s0, w[k]);
+            *cnt = 0;
+        }
     }
 }
 
-using SplitFn = void (*)(const uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t,
-                         uint32_t *, uint64_t, uint64_t, uint64_t, uint32_t *, JumpTables);
+using SplitFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t,
+                         uint32_t *, uint64_t, uint64_t, uint64_t, uint32_t *, uint32_t *,
+                         const uint64_t *, JumpTables);
 
 template <int KIND>
 SplitFn pick_split(int fmt, int hint)
@@ -197,7 +239,7 @@ constexpr int kSMs = 152;
 // jump that starts a segment costs about as much as this many rows: MWC a
 // few dozen Montgomery products, KISS those plus 32-column GF(2) products,
 // xor128 128-column products.
-int g_split_log2[3] = {6, 7, 10};
+int g_split_log2[3] = {6, 7, 8};
 // Threads that fill the device (CTAs of 256 at full occupancy).
 constexpr uint64_t kFillThreads = (uint64_t)kSMs * 1024;
 // CTA size of the kernels with row barriers: large CTAs leave fewer CTA
@@ -215,8 +257,14 @@ int fit_threads(int threads, uint64_t units)
 
 }  // namespace
 
+uint32_t split_max_segments(uint64_t n)
+{
+    const uint64_t threads = (n + 3) / 4;
+    return (uint32_t)std::min<uint64_t>(kFillThreads / std::max<uint64_t>(threads, 1), 65535);
+}
+
 bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per_thread,
-                uint64_t *rows, uint64_t *segments)
+                uint64_t max_segments, uint64_t *rows, uint64_t *segments)
 {
     const int l0 = g_split_log2[kind];
     if (l0 == 0 || streams == 0 || streams > kSplitMaxStreams || steps > (1ull << 31))
@@ -224,7 +272,8 @@ bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per
     const uint64_t threads = (streams + streams_per_thread - 1) / streams_per_thread;
     if (2 * threads > kFillThreads)
         return false;  // enough streams to fill the device already
-    const uint64_t want = std::min<uint64_t>(kFillThreads / threads, 65535);
+    const uint64_t want = std::min<uint64_t>(std::min<uint64_t>(kFillThreads / threads, 65535),
+                                             max_segments);
     uint64_t L = 1ull << l0;
     while (L < steps && (steps + L - 1) / L > want)
         L <<= 1;
@@ -261,26 +310,23 @@ int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
     const uint64_t main = count & ~(uint64_t)3;
     uint32_t *out = static_cast<uint32_t *>(p.out);
     uint64_t L = 0, S = 0;
-    if (p.split && sectors && split_plan(kind, count, p.steps, 4, &L, &S)) {
+    Gen *g = p.owner;
+    if (g && g->d_split && sectors &&
+        split_plan(kind, count, p.steps, 4, g->jmul_segs, &L, &S)) {
         JumpTables T{};
-        if (kind != RNG_MWC32) {
-            int e = jump_tables(&T);
-            if (e)
-                return e;
-        }
+        const uint64_t *jmul = nullptr;
+        int e = kind != RNG_MWC32 ? jump_tables(&T) : RNG_OK;
+        if (!e && kind != RNG_XOR128)
+            e = mwc_jump_table(g, L, st, &jmul);
+        if (e)
+            return e;
         SplitFn fn = kind == RNG_MWC32    ? pick_split<RNG_MWC32>(fmt, sh.hint)
                      : kind == RNG_XOR128 ? pick_split<RNG_XOR128>(fmt, sh.hint)
                                           : pick_split<RNG_KISS>(fmt, sh.hint);
         const dim3 grid((unsigned)((count / 4 + 255) / 256), (unsigned)S);
         fn<<<grid, 256, 0, st>>>(p.state, p.a, p.n, (uint32_t)p.steps, (uint32_t)L, out, p.ld,
-                                 p.s_begin, count, p.split, T);
-        int e = cuda_status(cudaGetLastError());
-        if (e)
-            return e;
-        const int W = words_of(kind);
-        return cuda_status(cudaMemcpy2DAsync(p.state + p.s_begin, p.n * 4, p.split + p.s_begin,
-                                             p.n * 4, count * 4, W, cudaMemcpyDeviceToDevice,
-                                             st));
+                                 p.s_begin, count, g->d_split, g->d_cnt, jmul, T);
+        return cuda_status(cudaGetLastError());
     }
     // Calls longer than 2^31 steps are cut into pieces (the kernels count
     // steps in 32 bits); the state carries from piece to piece.

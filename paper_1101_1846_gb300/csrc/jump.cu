@@ -83,6 +83,19 @@ __global__ void __launch_bounds__(128) build_tables(uint4 *t128, uint32_t *t32, 
     }
 }
 
+// Entry y*n + s: a_s^(y*rows) mod p_s in Montgomery form (0 for y = 0, the
+// segment that needs no jump).
+__global__ void __launch_bounds__(256)
+mwc_table_kernel(const uint32_t *__restrict__ a, uint64_t n, uint64_t rows, uint32_t segs,
+                 uint64_t *__restrict__ out)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * segs)
+        return;
+    const uint64_t y = i / n, s = i - y * n;
+    out[i] = y == 0 ? 0 : mwc_power(a[s], y * rows);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) jump_kernel(rng_device_view v, uint64_t k, JumpTables T)
 {
@@ -130,6 +143,24 @@ int jump_tables(JumpTables *out)
         d.t = JumpTables{t128, t32, tl};
     }
     *out = d.t;
+    return RNG_OK;
+}
+
+int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **table)
+{
+    if (!g->d_jmul || !g->d_a)
+        return set_error(RNG_ERR_ARG);
+    if (g->jmul_rows != rows) {
+        const uint64_t total = g->n * g->jmul_segs;
+        const uint64_t blocks = (total + 255) / 256;
+        mwc_table_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->d_a, g->n, rows, g->jmul_segs,
+                                                           g->d_jmul);
+        int e = cuda_status(cudaGetLastError());
+        if (e)
+            return e;
+        g->jmul_rows = rows;
+    }
+    *table = g->d_jmul;
     return RNG_OK;
 }
 

@@ -25,10 +25,9 @@ __device__ __forceinline__ uint64_t mwc_mul_a(uint64_t X, uint32_t a)
     return (uint64_t)a * (uint32_t)X + (X >> 32);
 }
 
-__device__ __forceinline__ void mwc_jump(uint32_t a, uint32_t &x, uint32_t &c, uint64_t k)
+// a^k mod p in Montgomery form, k >= 1.
+__device__ __forceinline__ uint64_t mwc_power(uint32_t a, uint64_t k)
 {
-    if (k == 0)
-        return;
     const uint64_t p = ((uint64_t)a << 32) - 1;
     const uint64_t ninv = ((uint64_t)a << 32) + 1;
     uint64_t A = (uint64_t)1 << 32;  // a^1 in Montgomery form: the top bit of k
@@ -37,9 +36,23 @@ __device__ __forceinline__ void mwc_jump(uint32_t a, uint32_t &x, uint32_t &c, u
         if ((k >> bit) & 1)
             A = mwc_mul_a(A, a);
     }
+    return A;
+}
+
+// (x, c) <- the state whose t is A t mod p, for A = a^k in Montgomery form.
+__device__ __forceinline__ void mwc_apply(uint64_t A, uint32_t a, uint32_t &x, uint32_t &c)
+{
+    const uint64_t p = ((uint64_t)a << 32) - 1;
+    const uint64_t ninv = ((uint64_t)a << 32) + 1;
     const uint64_t t = mont_mul(A, (uint64_t)a * x + c, p, ninv);  // a^k t mod p
     x = (uint32_t)(t / a);
     c = (uint32_t)(t - (uint64_t)x * a);
+}
+
+__device__ __forceinline__ void mwc_jump(uint32_t a, uint32_t &x, uint32_t &c, uint64_t k)
+{
+    if (k != 0)
+        mwc_apply(mwc_power(a, k), a, x, c);
 }
 
 // v <- M v for a 128 x 128 GF(2) matrix given by columns (word w of column j
@@ -86,24 +99,29 @@ __device__ __forceinline__ uint32_t gf2_apply32(const uint32_t *__restrict__ col
 }
 
 // Jumps G streams held as w[word][i] (the vector bodies' layout; G = 1 for
-// a single stream) with multipliers a[i] by k steps.
-template <int KIND, int G>
+// a single stream) with multipliers a[i] by k steps.  With MWC_DONE the MWC
+// words are left alone (the caller has applied a tabulated multiplier).
+template <int KIND, int G, bool MWC_DONE = false>
 __device__ __forceinline__ void jump_streams(uint32_t (&w)[4][4], const uint32_t (&a)[4],
                                              uint64_t k, const JumpTables &T)
 {
     if (k == 0)
         return;
     if constexpr (KIND == RNG_MWC32) {
+        if constexpr (!MWC_DONE) {
 #pragma unroll
-        for (int i = 0; i < G; ++i)
-            mwc_jump(a[i], w[0][i], w[1][i], k);
+            for (int i = 0; i < G; ++i)
+                mwc_jump(a[i], w[0][i], w[1][i], k);
+        }
     } else if constexpr (KIND == RNG_XOR128) {
         for (uint64_t r = k; r; r &= r - 1)
             gf2_apply128<G>(T.xor128 + 128 * (__ffsll((long long)r) - 1), w);
     } else {
+        if constexpr (!MWC_DONE) {
 #pragma unroll
-        for (int i = 0; i < G; ++i)
-            mwc_jump(a[i], w[0][i], w[1][i], k);
+            for (int i = 0; i < G; ++i)
+                mwc_jump(a[i], w[0][i], w[1][i], k);
+        }
         for (uint64_t r = k; r; r &= r - 1) {
             const int m = __ffsll((long long)r) - 1;
             const uint2 lc = __ldg(T.lcg + m);
@@ -116,9 +134,11 @@ __device__ __forceinline__ void jump_streams(uint32_t (&w)[4][4], const uint32_t
     }
 }
 
-// The same for one stream in an Engine.
+// The same for one stream in an Engine.  A != 0: the MWC part is multiplied
+// by A = a^k in Montgomery form (a tabulated power) instead of powering.
 template <int KIND>
-__device__ __forceinline__ void jump_engine(Engine<KIND> &e, uint64_t k, const JumpTables &T)
+__device__ __forceinline__ void jump_engine(Engine<KIND> &e, uint64_t k, const JumpTables &T,
+                                            uint64_t A = 0)
 {
     uint32_t w[4][4] = {};
     uint32_t a[4] = {};
@@ -138,7 +158,12 @@ __device__ __forceinline__ void jump_engine(Engine<KIND> &e, uint64_t k, const J
         w[3][0] = e.z;
         a[0] = e.a;
     }
-    jump_streams<KIND, 1>(w, a, k, T);
+    if (KIND != RNG_XOR128 && A != 0 && k != 0) {
+        mwc_apply(A, a[0], w[0][0], w[1][0]);
+        jump_streams<KIND, 1, true>(w, a, k, T);
+    } else {
+        jump_streams<KIND, 1>(w, a, k, T);
+    }
     if constexpr (KIND == RNG_MWC32) {
         e.x = w[0][0];
         e.c = w[1][0];

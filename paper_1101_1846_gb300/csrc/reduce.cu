@@ -10,8 +10,8 @@
 // One stream per thread, loaded with coalesced 4-byte accesses across the
 // warp.  Few streams with long sequences are split into segments of 2^l
 // rows (split_plan; grid y = segment) that start from jumped states; their
-// results are added into out with 64-bit atomics (exact, in any order) and
-// the last segment's state goes to the scratch and is copied back.
+// results are added into out with 64-bit atomics (exact, in any order), and
+// the final state is written back by the last arrival, as in gen_split.
 #include "jump.cuh"
 
 namespace gbrng {
@@ -45,44 +45,72 @@ __device__ __forceinline__ uint64_t consume(Engine<KIND> &e, uint64_t m)
     return acc;
 }
 
-template <int KIND, int OP>
+// SPLIT = false: one segment (grid y = 1), the whole call per thread.
+template <int KIND, int OP, bool SPLIT>
 __global__ void __launch_bounds__(kThreads)
 reduce_kernel(rng_device_view v, uint64_t steps, uint64_t rows, uint64_t *__restrict__ out,
-              uint32_t *__restrict__ final_state, JumpTables T)
+              uint32_t *__restrict__ stash, uint32_t *__restrict__ counters,
+              const uint64_t *__restrict__ jmul, JumpTables T)
 {
     const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= v.n_streams)
         return;
     Engine<KIND> e;
     e.load(v, s);
-    if (gridDim.y == 1) {
+    if constexpr (!SPLIT) {
         out[s] = consume<OP>(e, steps);
         e.store(v, s);
         return;
     }
+    // Split: the same arrival count as gen_split (one counter per stream).
+    const uint32_t segs = gridDim.y;
+    const uint64_t n = v.n_streams;
+    uint32_t *state = static_cast<uint32_t *>(v.state);
+    __threadfence();
+    uint32_t *cnt = counters + s;
+    if (atomicAdd(cnt, 1u) == segs) {
+        __threadfence();
+        for (int k = 0; k < v.state_words; ++k)
+            state[k * n + s] = __ldcg(stash + k * n + s);
+        *cnt = 0;
+    }
     const uint64_t first = (uint64_t)blockIdx.y * rows;
     const uint64_t mine = steps - first < rows ? steps - first : rows;
-    jump_engine<KIND>(e, first, T);
+    const uint64_t A = (KIND != RNG_XOR128 && blockIdx.y > 0) ? jmul[blockIdx.y * n + s] : 0;
+    jump_engine<KIND>(e, first, T, A);
     atomicAdd(reinterpret_cast<unsigned long long *>(out + s),
               (unsigned long long)consume<OP>(e, mine));
-    if (blockIdx.y == gridDim.y - 1) {
+    if (blockIdx.y == segs - 1) {
         rng_device_view f = v;
-        f.state = final_state;
+        f.state = stash;
         e.store(f, s);
+        __threadfence();
+        if (atomicAdd(cnt, 1u) == segs) {
+            e.store(v, s);
+            *cnt = 0;
+        }
     }
 }
 
 using ReduceFn = void (*)(rng_device_view, uint64_t, uint64_t, uint64_t *, uint32_t *,
-                          JumpTables);
+                          uint32_t *, const uint64_t *, JumpTables);
 
-template <int KIND>
+template <int KIND, bool SPLIT>
 ReduceFn pick(int op)
 {
     if (op == RNG_SUM_U32)
-        return reduce_kernel<KIND, RNG_SUM_U32>;
+        return reduce_kernel<KIND, RNG_SUM_U32, SPLIT>;
     if (op == RNG_SUM_U24)
-        return reduce_kernel<KIND, RNG_SUM_U24>;
-    return reduce_kernel<KIND, RNG_DISC>;
+        return reduce_kernel<KIND, RNG_SUM_U24, SPLIT>;
+    return reduce_kernel<KIND, RNG_DISC, SPLIT>;
+}
+
+template <bool SPLIT>
+ReduceFn pick_kind(int kind, int op)
+{
+    return kind == RNG_MWC32    ? pick<RNG_MWC32, SPLIT>(op)
+           : kind == RNG_XOR128 ? pick<RNG_XOR128, SPLIT>(op)
+                                : pick<RNG_KISS, SPLIT>(op);
 }
 
 }  // namespace
@@ -103,30 +131,29 @@ extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, 
     cudaStream_t st = g->stream;
     uint64_t *o = static_cast<uint64_t *>(out);
     rng_device_view v{g->kind, g->device, g->words, g->n, g->d_state, g->d_a};
-    ReduceFn fn = g->kind == RNG_MWC32    ? pick<RNG_MWC32>(op)
-                  : g->kind == RNG_XOR128 ? pick<RNG_XOR128>(op)
-                                          : pick<RNG_KISS>(op);
     uint64_t rows = n_per_stream, segs = 1;
     // pairs never straddle segments: split rows are powers of two >= 2
-    const bool split = g->d_split && split_plan(g->kind, g->n, n_per_stream, 1, &rows, &segs);
+    const bool split = g->d_split &&
+                       split_plan(g->kind, g->n, n_per_stream, 1, g->jmul_segs, &rows, &segs);
     if (!split) {
         rows = n_per_stream;
         segs = 1;
     }
+    ReduceFn fn = split ? pick_kind<true>(g->kind, op) : pick_kind<false>(g->kind, op);
     JumpTables T{};
+    const uint64_t *jmul = nullptr;
     int status = RNG_OK;
     if (split && g->kind != RNG_MWC32)
         status = jump_tables(&T);
+    if (!status && split && g->kind != RNG_XOR128)
+        status = mwc_jump_table(g, rows, st, &jmul);
     if (!status && split)
         status = cuda_status(cudaMemsetAsync(o, 0, g->n * 8, st));
     if (!status) {
         const dim3 grid((unsigned)((g->n + kThreads - 1) / kThreads), (unsigned)segs);
-        fn<<<grid, kThreads, 0, st>>>(v, n_per_stream, rows, o, g->d_split, T);
+        fn<<<grid, kThreads, 0, st>>>(v, n_per_stream, rows, o, g->d_split, g->d_cnt, jmul, T);
         status = cuda_status(cudaGetLastError());
     }
-    if (!status && split)
-        status = cuda_status(cudaMemcpyAsync(g->d_state, g->d_split, (size_t)g->words * g->n * 4,
-                                             cudaMemcpyDeviceToDevice, st));
     if (prev >= 0 && prev != g->device)
         cudaSetDevice(prev);
     return status;

@@ -78,7 +78,7 @@ class split_set:
 @pytest.mark.parametrize("split", [True, False], ids=["split", "whole"])
 def test_reduce_equals_oracle_and_carries_state(kind, op, split):
     n, seed = 1003, 21
-    with split_set(kind, 0 if not split else {0: 6, 1: 10, 2: 7}[kind]):
+    with split_set(kind, 0 if not split else {0: 6, 1: 8, 2: 7}[kind]):
         _reduce_twice_then_generate(kind, op, n, seed)
 
 
