@@ -8,9 +8,13 @@ reference legs may import this package; the product library never does and
 shares no code with it.
 
 Kinds: 0 = MWC base 2^32 (Eq. 2-3), 1 = xor128 (Marsaglia 2003), 2 = KISS
-(MWC + xorshift32 of Eq. 6 + LCG of Eq. 7, summed mod 2^32).
+(MWC + xorshift32 of Eq. 6 + LCG of Eq. 7, summed mod 2^32), and the paper's
+own generators: 3 = two base-2^16 MWCs joined as (z << 16) + w, 4 = Panneton's
+r = 8 XorShift (Eq. 5), 5 = KISS as (MWC16X2 xor LCG) + xorshift32.
 Formats: 0 = uint32, 1 = float32 uniform (u >> 8) * 2^-24.
-State: four uint32 words per stream (see ``oracle.h``).
+State: words(kind) uint32 words per stream (8 for kind 4, else 4; see
+``oracle.h``); kinds 0 and 2 take one multiplier per stream, kinds 3 and 5
+one packed pair of 16-bit multipliers.
 """
 from __future__ import annotations
 
@@ -28,8 +32,14 @@ BUILD = HERE / "_build"
 LIB = BUILD / "liboracle.so"
 SOURCES = [HERE / "oracle.c", HERE / "oracle.h"]
 
-MWC, XOR128, KISS = 0, 1, 2
+MWC, XOR128, KISS, MWC16X2, XORSHIFT8, KISS_XOR = 0, 1, 2, 3, 4, 5
 U32, F32 = 0, 1
+HAS_MULT = (MWC, KISS, MWC16X2, KISS_XOR)
+
+
+def words(kind: int) -> int:
+    """State words per stream in the oracle's layout."""
+    return 8 if kind == XORSHIFT8 else 4
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -91,6 +101,12 @@ def _load(path: Path):
         "oracle_is_safe_multiplier": (i32, [u64, i32]),
         "oracle_multipliers": (u64, [i32, u64, u64, _u32p]),
         "oracle_multipliers_range": (u64, [i32, u64, u64, _u32p, u64]),
+        "oracle_mwc16_pairs": (u64, [u64, _u32p]),
+        "oracle_mwc16x2_step": (u32, [u32, _u32p]),
+        "oracle_xorshift8_step": (u32, [_u32p]),
+        "oracle_kiss_xor_step": (u32, [u32, _u32p]),
+        "oracle_state_words": (i32, [i32]),
+        "oracle_xorshift8_jump": (None, [_u32p, u64]),
         "oracle_splitmix64": (u64, [_u64p]),
         "oracle_seed_stream": (None, [i32, u32, u64, u64, _u32p]),
         "oracle_seed_streams": (None, [i32, _u32p, u64, _u64p, u64, _u32p]),
@@ -203,13 +219,13 @@ def splitmix64(z: int) -> tuple[int, int]:
 
 def seed_streams(kind: int, a: np.ndarray | None, seed: int,
                  s_ids: np.ndarray) -> np.ndarray:
-    """Initial state (n, 4) uint32 of the streams with indices s_ids; a[i]
-    is the multiplier of stream s_ids[i]."""
+    """Initial state (n, words(kind)) uint32 of the streams with indices
+    s_ids; a[i] is the multiplier (or packed pair) of stream s_ids[i]."""
     s_ids = np.ascontiguousarray(s_ids, dtype=np.uint64)
     n = len(s_ids)
-    st = np.zeros((n, 4), np.uint32)
+    st = np.zeros((n, words(kind)), np.uint32)
     ap = None
-    if kind != XOR128:
+    if kind in HAS_MULT:
         a = np.ascontiguousarray(a, dtype=np.uint32)
         assert len(a) == n
         ap = _p32(a)
@@ -251,6 +267,40 @@ def kiss_step(a: int, st) -> tuple[int, list]:
     return int(out), list(arr)
 
 
+def mwc16x2_step(a_pair: int, st) -> tuple[int, list]:
+    arr = (ctypes.c_uint32 * 2)(*[int(v) for v in st[:2]])
+    out = lib().oracle_mwc16x2_step(a_pair, arr)
+    return int(out), list(arr)
+
+
+def xorshift8_step(st) -> tuple[int, list]:
+    arr = (ctypes.c_uint32 * 8)(*[int(v) for v in st])
+    out = lib().oracle_xorshift8_step(arr)
+    return int(out), list(arr)
+
+
+def kiss_xor_step(a_pair: int, st) -> tuple[int, list]:
+    arr = _st(st)
+    out = lib().oracle_kiss_xor_step(a_pair, arr)
+    return int(out), list(arr)
+
+
+def mwc16_pairs(k: int) -> np.ndarray:
+    """The first k packed multiplier pairs of the paper's two-part MWC."""
+    out = np.zeros(k, np.uint32)
+    got = lib().oracle_mwc16_pairs(k, _p32(out))
+    return out[:got]
+
+
+def multipliers_for(kind: int, n: int) -> np.ndarray | None:
+    """The per-stream multipliers (or packed pairs) of the first n streams."""
+    if kind in (MWC, KISS):
+        return multipliers(n, 32)
+    if kind in (MWC16X2, KISS_XOR):
+        return mwc16_pairs(n)
+    return None
+
+
 def to_unit_f32(u: int) -> float:
     return float(np.float32(lib().oracle_to_unit_f32(u)))
 
@@ -262,10 +312,11 @@ def generate(kind: int, a: np.ndarray | None, state: np.ndarray,
     with out of shape (n_per_stream, n_streams): out[j, s] is output j of
     stream s (the stream-interleaved layout)."""
     state = np.array(state, dtype=np.uint32, order="C", copy=True)
+    assert state.shape[1] == words(kind)
     n = state.shape[0]
     out = np.zeros((n_per_stream, n), np.uint32 if fmt == U32 else np.float32)
     ap = None
-    if kind != XOR128:
+    if kind in HAS_MULT:
         a = np.ascontiguousarray(a, dtype=np.uint32)
         assert len(a) >= n
         ap = _p32(a)
@@ -277,6 +328,7 @@ def generate(kind: int, a: np.ndarray | None, state: np.ndarray,
 def stream(kind: int, a: int, st, n: int, fmt: int) -> tuple[np.ndarray, np.ndarray]:
     """n outputs of one stream, contiguous; returns (out, new_state)."""
     arr = np.array(st, dtype=np.uint32)
+    assert len(arr) == words(kind)
     out = np.zeros(n, np.uint32 if fmt == U32 else np.float32)
     lib().oracle_stream(kind, a, _p32(arr), n, fmt,
                         out.ctypes.data_as(ctypes.c_void_p))
@@ -307,10 +359,11 @@ def reduce(kind: int, a: np.ndarray | None, state: np.ndarray, n_per_stream: int
     """Every stream advances n_per_stream steps; returns (out, new_state)
     with out[s] the consumer `op` over stream s's outputs (uint64)."""
     state = np.array(state, dtype=np.uint32, order="C", copy=True)
+    assert state.shape[1] == words(kind)
     n = state.shape[0]
     out = np.zeros(n, np.uint64)
     ap = None
-    if kind != XOR128:
+    if kind in HAS_MULT:
         a = np.ascontiguousarray(a, dtype=np.uint32)
         assert len(a) >= n
         ap = _p32(a)
@@ -321,8 +374,9 @@ def reduce(kind: int, a: np.ndarray | None, state: np.ndarray, n_per_stream: int
 
 # ----------------------------------------------------------------- jumps
 def jump(kind: int, a: int, st, k: int) -> np.ndarray:
-    """State of one stream k steps after st (4 uint32 words)."""
+    """State of one stream k steps after st (words(kind) uint32 words)."""
     arr = np.array(st, dtype=np.uint32)
+    assert len(arr) == words(kind)
     lib().oracle_jump(kind, int(a), _p32(arr), int(k))
     return arr
 

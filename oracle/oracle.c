@@ -27,6 +27,17 @@
  *                                    disc by integer square roots)
  *   jump-ahead ..................... pinned (equal to stepping; periods of
  *                                    each part reached by one jump)
+ *   the paper's own generators:
+ *     two-part base-2^16 MWC ....... pinned (parts are the pinned base-2^16
+ *                                    step; Lehmer closed form of the joined
+ *                                    output; pairs in lexicographic order);
+ *                                    joining by + rather than | is the reading
+ *                                    the paper's operation count fixes
+ *     r = 8 XorShift (Eq. 5) ....... pinned (period 2^256-1 over GF(2); the
+ *                                    five lags); the order of the factors of
+ *                                    (I+L^24)(I+R^7) is parity unpinned: both
+ *                                    orders have full period
+ *     KISS, xor form ............... pinned (parts stepped on their own)
  */
 #include "oracle.h"
 
@@ -187,6 +198,22 @@ uint64_t oracle_multipliers_range(int log2b, uint64_t a_hi, uint64_t a_lo,
     return found;
 }
 
+/* Multiplier pairs of the paper's two-part MWC: the first k pairs (i, j),
+ * i < j, of the 392 base-2^16 multipliers (largest first) in lexicographic
+ * order, packed as table[i] | table[j] << 16 (parametrisation by pairs of
+ * multipliers, Methods / MWC).  Returns how many were written (at most
+ * 392 * 391 / 2). */
+uint64_t oracle_mwc16_pairs(uint64_t k, uint32_t *out)
+{
+    uint32_t table[512];
+    uint64_t m = oracle_multipliers(16, 0xFFFF, 512, table);
+    uint64_t found = 0;
+    for (uint64_t i = 0; i < m && found < k; ++i)
+        for (uint64_t j = i + 1; j < m && found < k; ++j)
+            out[found++] = table[i] | (table[j] << 16);
+    return found;
+}
+
 /* ------------------------------------------------------------------ */
 /* Seeding.  The paper gives every thread its own seeds (parametrisation,
  * Sec. "Parallelizing RNGs" and the MWC/KISS kernel descriptions) without
@@ -223,11 +250,57 @@ static void seed_mwc(uint32_t a, uint64_t *z, uint32_t *x, uint32_t *c)
     }
 }
 
+/* The paper's MWC pair from one draw: (x, c) of the first part from bits
+ * 0-15 and 16-31 (c reduced below a1), of the second from bits 32-47 and
+ * 48-63 (c below a2); drawn again while either part is a fixed point. */
+static void seed_mwc16x2(uint32_t a_pair, uint64_t *z, uint32_t *zw)
+{
+    uint32_t a1 = a_pair & 0xFFFFu, a2 = a_pair >> 16;
+    for (;;) {
+        uint64_t r = oracle_splitmix64(z);
+        uint32_t x1 = (uint32_t)(r & 0xFFFFu), c1 = (uint32_t)((r >> 16) & 0xFFFFu) % a1;
+        uint32_t x2 = (uint32_t)((r >> 32) & 0xFFFFu), c2 = (uint32_t)(r >> 48) % a2;
+        int bad1 = (x1 == 0 && c1 == 0) || (x1 == 0xFFFFu && c1 == a1 - 1);
+        int bad2 = (x2 == 0 && c2 == 0) || (x2 == 0xFFFFu && c2 == a2 - 1);
+        if (!bad1 && !bad2) {
+            zw[0] = x1 | (c1 << 16);
+            zw[1] = x2 | (c2 << 16);
+            return;
+        }
+    }
+}
+
 void oracle_seed_stream(int kind, uint32_t a, uint64_t seed, uint64_t s,
-                        uint32_t st[4])
+                        uint32_t *st)
 {
     uint64_t z = seed + s;
-    memset(st, 0, 4 * sizeof(uint32_t));
+    memset(st, 0, (size_t)oracle_state_words(kind) * sizeof(uint32_t));
+    if (kind == 3) {
+        seed_mwc16x2(a, &z, st);
+        return;
+    }
+    if (kind == 4) {
+        for (;;) {
+            uint32_t any = 0;
+            for (int i = 0; i < 4; ++i) {
+                uint64_t r = oracle_splitmix64(&z);
+                st[2 * i] = lo32(r);
+                st[2 * i + 1] = hi32(r);
+                any |= st[2 * i] | st[2 * i + 1];
+            }
+            if (any)
+                return;
+        }
+    }
+    if (kind == 5) {
+        seed_mwc16x2(a, &z, st);
+        uint64_t r = oracle_splitmix64(&z);
+        st[2] = lo32(r);
+        st[3] = hi32(r);
+        while (st[2] == 0)
+            st[2] = lo32(oracle_splitmix64(&z));
+        return;
+    }
     if (kind == 0) {
         seed_mwc(a, &z, &st[0], &st[1]);
     } else if (kind == 1) {
@@ -311,14 +384,76 @@ uint32_t oracle_kiss_step(uint32_t a, uint32_t st[4])
     return (uint32_t)(((uint64_t)m + y + z) % ((uint64_t)1 << 32));
 }
 
-uint32_t oracle_step(int kind, uint32_t a, uint32_t st[4])
+/* The paper's own MWC (Methods, "multiply-with-carry"): two base-2^16
+ * MWCs with 16-bit multipliers a1 = a_pair & 0xFFFF and a2 = a_pair >> 16.
+ * Each is kept in one 32-bit word z = x + c 2^16 (x the last value, c the
+ * carry); one step of Eq. 2-3 with b = 2^16 maps it to a (z mod 2^16) +
+ * (z div 2^16).  The output joins the two new words as (z << 16) + w mod
+ * 2^32: three shifts, two ands, two multiplies and three adds, the
+ * operation count the paper gives for its loop. */
+uint32_t oracle_mwc16x2_step(uint32_t a_pair, uint32_t st[2])
+{
+    uint32_t a1 = a_pair & 0xFFFFu, a2 = a_pair >> 16;
+    uint32_t x = st[0] & 0xFFFFu, c = st[0] >> 16;
+    oracle_mwc_step(a1, &x, &c, 16);
+    st[0] = x | (c << 16);
+    x = st[1] & 0xFFFFu;
+    c = st[1] >> 16;
+    oracle_mwc_step(a2, &x, &c, 16);
+    st[1] = x | (c << 16);
+    return (uint32_t)((((uint64_t)st[0] << 16) + st[1]) % ((uint64_t)1 << 32));
+}
+
+/* Eq. 5, Panneton's XorShift with r = 8 words and s = 7 xorshifts:
+ * st = (v_{n-8}, ..., v_{n-1});
+ *   v_n = (I+L^9)(I+L^13) v_{n-1} + (I+L^7) v_{n-4} + (I+R^3) v_{n-5}
+ *       + (I+R^10) v_{n-7} + (I+L^24)(I+R^7) v_{n-8}
+ * over GF(2) (+ is xor), each product applied right to left as in Eq. 4's
+ * v_i = sum A_j v_{i-j}; the words shift down and v_n, the output, enters
+ * at the top. */
+uint32_t oracle_xorshift8_step(uint32_t st[8])
+{
+    uint32_t t1 = st[7] ^ (st[7] << 13);
+    t1 ^= t1 << 9;
+    uint32_t t4 = st[4] ^ (st[4] << 7);
+    uint32_t t5 = st[3] ^ (st[3] >> 3);
+    uint32_t t7 = st[1] ^ (st[1] >> 10);
+    uint32_t t8 = st[0] ^ (st[0] >> 7);
+    t8 ^= t8 << 24;
+    uint32_t v = t1 ^ t4 ^ t5 ^ t7 ^ t8;
+    for (int i = 0; i < 7; ++i)
+        st[i] = st[i + 1];
+    st[7] = v;
+    return v;
+}
+
+/* KISS as the paper's Background section combines it: the MWC and LCG
+ * values are xored and the XorShift value is added, with the paper's own
+ * two-part MWC: ((MWC xor LCG) + xorshift32) mod 2^32.  State {z, w, y, z_lcg}. */
+uint32_t oracle_kiss_xor_step(uint32_t a_pair, uint32_t st[4])
+{
+    uint32_t m = oracle_mwc16x2_step(a_pair, st);
+    uint32_t y = oracle_xorshift32_step(&st[2]);
+    uint32_t z = oracle_lcg_step(&st[3]);
+    return (uint32_t)(((uint64_t)(m ^ z) + y) % ((uint64_t)1 << 32));
+}
+
+uint32_t oracle_step(int kind, uint32_t a, uint32_t *st)
 {
     if (kind == 0)
         return oracle_mwc_step(a, &st[0], &st[1], 32);
     if (kind == 1)
         return oracle_xor128_step(st);
-    return oracle_kiss_step(a, st);
+    if (kind == 2)
+        return oracle_kiss_step(a, st);
+    if (kind == 3)
+        return oracle_mwc16x2_step(a, st);
+    if (kind == 4)
+        return oracle_xorshift8_step(st);
+    return oracle_kiss_xor_step(a, st);
 }
+
+int oracle_state_words(int kind) { return kind == 4 ? 8 : 4; }
 
 /* Uniform in [0, 1): the top 24 bits of u as an integer times 2^-24.  Both
  * the conversion (a 24-bit integer) and the power-of-two scaling are exact
@@ -329,7 +464,7 @@ float oracle_to_unit_f32(uint32_t u)
 }
 
 /* One stream: n outputs written contiguously, state advanced in place. */
-void oracle_stream(int kind, uint32_t a, uint32_t st[4], uint64_t n, int fmt,
+void oracle_stream(int kind, uint32_t a, uint32_t *st, uint64_t n, int fmt,
                    void *out)
 {
     for (uint64_t j = 0; j < n; ++j) {
@@ -342,13 +477,14 @@ void oracle_stream(int kind, uint32_t a, uint32_t st[4], uint64_t n, int fmt,
 }
 
 /* One generate call over all streams: output j of stream s goes to
- * out[j * n_streams + s]; state holds 4 words per stream (st[4*s + w]). */
+ * out[j * n_streams + s]; state holds W = oracle_state_words(kind) words per
+ * stream (st[W*s + w]). */
 void oracle_generate(int kind, uint64_t n_streams, const uint32_t *a,
                      uint32_t *state, uint64_t n_per_stream, int fmt,
                      void *out)
 {
     for (uint64_t s = 0; s < n_streams; ++s) {
-        uint32_t *st = state + 4 * s;
+        uint32_t *st = state + (uint64_t)oracle_state_words(kind) * s;
         uint32_t as = a ? a[s] : 0;
         for (uint64_t j = 0; j < n_per_stream; ++j) {
             uint32_t u = oracle_step(kind, as, st);
@@ -410,7 +546,8 @@ void oracle_seed_streams(int kind, const uint32_t *a, uint64_t seed,
                          const uint64_t *s_ids, uint64_t n, uint32_t *st)
 {
     for (uint64_t i = 0; i < n; ++i)
-        oracle_seed_stream(kind, a ? a[i] : 0, seed, s_ids[i], st + 4 * i);
+        oracle_seed_stream(kind, a ? a[i] : 0, seed, s_ids[i],
+                           st + (uint64_t)oracle_state_words(kind) * i);
 }
 
 /* ------------------------------------------------------------------ */
@@ -458,8 +595,8 @@ uint64_t oracle_disc_count(const uint32_t *u, uint64_t n)
     return inside;
 }
 
-/* Every stream advances n_per_stream steps (state in place, 4 words per
- * stream as in oracle_generate); out[s] is the chosen consumer applied to
+/* Every stream advances n_per_stream steps (state in place, laid out as in
+ * oracle_generate); out[s] is the chosen consumer applied to
  * stream s's outputs: op 0 = oracle_sum_u32, 1 = oracle_sum_u24,
  * 2 = oracle_disc_count.  Returns 0, or -1 if the scratch row cannot be
  * allocated. */
@@ -471,7 +608,8 @@ int oracle_reduce(int kind, uint64_t n_streams, const uint32_t *a,
     if (!row)
         return -1;
     for (uint64_t s = 0; s < n_streams; ++s) {
-        oracle_stream(kind, a ? a[s] : 0, state + 4 * s, n_per_stream, 0, row);
+        oracle_stream(kind, a ? a[s] : 0, state + (uint64_t)oracle_state_words(kind) * s,
+                      n_per_stream, 0, row);
         if (op == 0)
             out[s] = oracle_sum_u32(row, n_per_stream);
         else if (op == 1)
@@ -511,25 +649,26 @@ void oracle_mwc_jump(uint32_t a, uint32_t *x, uint32_t *c, uint64_t k,
  * is the image of the unit vector e_j under the step. */
 typedef struct {
     int nbits;
-    uint32_t col[128][4];
+    uint32_t col[256][8];
 } gf2mat;
 
-static void gf2_apply(const gf2mat *m, const uint32_t v[4], uint32_t out[4])
+static void gf2_apply(const gf2mat *m, const uint32_t v[8], uint32_t out[8])
 {
-    uint32_t r[4] = {0, 0, 0, 0};
+    uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = 0; j < m->nbits; ++j) {
         if ((v[j / 32] >> (j % 32)) & 1u) {
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < 8; ++w)
                 r[w] ^= m->col[j][w];
         }
     }
-    memcpy(out, r, sizeof(r));
+    memcpy(out, r, (size_t)((m->nbits + 31) / 32) * sizeof(uint32_t));
 }
 
 /* out = a * b: column j of the product is a applied to column j of b. */
 static void gf2_mul(const gf2mat *a, const gf2mat *b, gf2mat *out)
 {
     gf2mat r;
+    memset(&r, 0, sizeof(r));
     r.nbits = a->nbits;
     for (int j = 0; j < a->nbits; ++j)
         gf2_apply(a, b->col[j], r.col[j]);
@@ -570,6 +709,18 @@ static void xor128_matrix(gf2mat *m)
     }
 }
 
+static void xorshift8_matrix(gf2mat *m)
+{
+    memset(m, 0, sizeof(*m));
+    m->nbits = 256;
+    for (int j = 0; j < 256; ++j) {
+        uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        st[j / 32] = 1u << (j % 32);
+        oracle_xorshift8_step(st);
+        memcpy(m->col[j], st, sizeof(st));
+    }
+}
+
 static void xorshift32_matrix(gf2mat *m)
 {
     memset(m, 0, sizeof(*m));
@@ -581,22 +732,32 @@ static void xorshift32_matrix(gf2mat *m)
     }
 }
 
+/* The matrices are large (8 KB each): kept in static storage. */
+static gf2mat g_m, g_mk;
+
 void oracle_xor128_jump(uint32_t st[4], uint64_t k)
 {
-    gf2mat m, mk;
-    xor128_matrix(&m);
-    gf2_pow(&m, k, &mk);
-    gf2_apply(&mk, st, st);
+    uint32_t v[8] = {st[0], st[1], st[2], st[3], 0, 0, 0, 0};
+    xor128_matrix(&g_m);
+    gf2_pow(&g_m, k, &g_mk);
+    gf2_apply(&g_mk, v, v);
+    memcpy(st, v, 4 * sizeof(uint32_t));
 }
 
 void oracle_xorshift32_jump(uint32_t *y, uint64_t k)
 {
-    gf2mat m, mk;
-    xorshift32_matrix(&m);
-    gf2_pow(&m, k, &mk);
-    uint32_t v[4] = {*y, 0, 0, 0};
-    gf2_apply(&mk, v, v);
+    uint32_t v[8] = {*y, 0, 0, 0, 0, 0, 0, 0};
+    xorshift32_matrix(&g_m);
+    gf2_pow(&g_m, k, &g_mk);
+    gf2_apply(&g_mk, v, v);
     *y = v[0];
+}
+
+void oracle_xorshift8_jump(uint32_t st[8], uint64_t k)
+{
+    xorshift8_matrix(&g_m);
+    gf2_pow(&g_m, k, &g_mk);
+    gf2_apply(&g_mk, st, st);
 }
 
 /* Eq. 7's map z -> A z + C (mod 2^32) applied k times.  Two affine maps
@@ -618,14 +779,32 @@ void oracle_lcg_jump(uint32_t *z, uint64_t k)
     *z = (uint32_t)((RA * (uint64_t)(*z) + RC) % m);
 }
 
-void oracle_jump(int kind, uint32_t a, uint32_t st[4], uint64_t k)
+/* One base-2^16 MWC packed as x | c << 16 (see oracle_mwc16x2_step). */
+static void mwc16_jump(uint32_t a, uint32_t *z, uint64_t k)
+{
+    uint32_t x = *z & 0xFFFFu, c = *z >> 16;
+    oracle_mwc_jump(a, &x, &c, k, 16);
+    *z = x | (c << 16);
+}
+
+void oracle_jump(int kind, uint32_t a, uint32_t *st, uint64_t k)
 {
     if (kind == 0) {
         oracle_mwc_jump(a, &st[0], &st[1], k, 32);
     } else if (kind == 1) {
         oracle_xor128_jump(st, k);
-    } else {
+    } else if (kind == 2) {
         oracle_mwc_jump(a, &st[0], &st[1], k, 32);
+        oracle_xorshift32_jump(&st[2], k);
+        oracle_lcg_jump(&st[3], k);
+    } else if (kind == 3) {
+        mwc16_jump(a & 0xFFFFu, &st[0], k);
+        mwc16_jump(a >> 16, &st[1], k);
+    } else if (kind == 4) {
+        oracle_xorshift8_jump(st, k);
+    } else {
+        mwc16_jump(a & 0xFFFFu, &st[0], k);
+        mwc16_jump(a >> 16, &st[1], k);
         oracle_xorshift32_jump(&st[2], k);
         oracle_lcg_jump(&st[3], k);
     }

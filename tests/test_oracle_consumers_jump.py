@@ -85,8 +85,9 @@ def check_sum_means():
 
 def check_reduce_advances_like_generate():
     n, steps = 5, 777
-    for kind in (oracle.MWC, oracle.XOR128, oracle.KISS):
-        a = oracle.multipliers(n, 32) if kind != oracle.XOR128 else None
+    for kind in (oracle.MWC, oracle.XOR128, oracle.KISS, oracle.MWC16X2, oracle.XORSHIFT8,
+                 oracle.KISS_XOR):
+        a = oracle.multipliers_for(kind, n)
         st = oracle.seed_streams(kind, a, 3, np.arange(n))
         u, st_gen = oracle.generate(kind, a, st, steps, oracle.U32)
         for op, fn in ((oracle.SUM_U32, oracle.sum_u32), (oracle.SUM_U24, oracle.sum_u24),
@@ -120,30 +121,35 @@ def test_reduce_advances_like_generate():
 JUMPS = (0, 1, 2, 3, 31, 32, 33, 1000, (1 << 17) + 5)
 
 
+ALL_KINDS = (oracle.MWC, oracle.XOR128, oracle.KISS, oracle.MWC16X2, oracle.XORSHIFT8,
+             oracle.KISS_XOR)
+
+
 def check_jump_equals_stepping():
     """The state after jump(k) equals the state after k single steps."""
     n = 3
-    for kind in (oracle.MWC, oracle.XOR128, oracle.KISS):
-        a = oracle.multipliers(n, 32)
-        st = oracle.seed_streams(kind, a if kind != oracle.XOR128 else None, 11,
-                                 np.arange(n))
+    for kind in ALL_KINDS:
+        a = oracle.multipliers_for(kind, n)
+        st = oracle.seed_streams(kind, a, 11, np.arange(n))
         for s in range(n):
             for k in JUMPS:
-                _, stepped = oracle.stream(kind, int(a[s]), st[s], k, oracle.U32)
-                jumped = oracle.jump(kind, int(a[s]), st[s], k)
+                ai = int(a[s]) if a is not None else 0
+                _, stepped = oracle.stream(kind, ai, st[s], k, oracle.U32)
+                jumped = oracle.jump(kind, ai, st[s], k)
                 assert np.array_equal(stepped, jumped), (kind, s, k)
 
 
 def check_jump_composes():
     rng = np.random.Generator(np.random.PCG64(8))
-    a = oracle.multipliers(2, 32)
-    for kind in (oracle.MWC, oracle.XOR128, oracle.KISS):
-        st = oracle.seed_streams(kind, a if kind != oracle.XOR128 else None, 5, np.arange(2))
+    for kind in ALL_KINDS:
+        a = oracle.multipliers_for(kind, 2)
+        a0 = int(a[0]) if a is not None else 0
+        st = oracle.seed_streams(kind, a, 5, np.arange(2))
         for _ in range(4):
             j = int(rng.integers(0, 1 << 62)) * 3
             k = int(rng.integers(0, 1 << 62))
-            two = oracle.jump(kind, int(a[0]), oracle.jump(kind, int(a[0]), st[0], j), k)
-            one = oracle.jump(kind, int(a[0]), st[0], (j + k) % M64)
+            two = oracle.jump(kind, a0, oracle.jump(kind, a0, st[0], j), k)
+            one = oracle.jump(kind, a0, st[0], (j + k) % M64)
             assert np.array_equal(two, one), (kind, j, k)
 
 

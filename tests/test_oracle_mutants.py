@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import test_oracle_consumers_jump as cj
+import test_oracle_paper_variants as pv
 import test_oracle_pins as pins
 
 SRC = (oracle.HERE / "oracle.c").read_text()
@@ -63,12 +64,27 @@ MUTANTS = [
      "*c = (uint32_t)(t / a);\n    *x = (uint32_t)(t % a);", cj.check_jump_equals_stepping),
     ("MWC jump multiplies by b^k", "oracle_powmod_u64(a, k, p)",
      "oracle_powmod_u64((uint64_t)1 << log2b, k, p)", cj.check_mwc_jump_lehmer),
-    ("GF(2) apply drops the top word", "for (int w = 0; w < 4; ++w)\n                r[w] ^= m->col[j][w];",
+    ("GF(2) apply drops the top word", "for (int w = 0; w < 8; ++w)\n                r[w] ^= m->col[j][w];",
      "for (int w = 0; w < 3; ++w)\n                r[w] ^= m->col[j][w];", cj.check_jump_equals_stepping),
     ("GF(2) power uses the wrong bit", "if (k & 1)\n            gf2_mul(&result, &base, &result);",
      "if (k & 2)\n            gf2_mul(&result, &base, &result);", cj.check_jump_periods),
     ("LCG jump drops the increment", "RC = (BA * RC + BC) % m;", "RC = (BA * RC) % m;",
      cj.check_jump_equals_stepping),
+    ("r=8 XorShift shift 9->8", "t1 ^= t1 << 9;", "t1 ^= t1 << 8;",
+     pv.check_xorshift8_full_period),
+    ("r=8 XorShift lag 5 read as lag 6", "uint32_t t5 = st[3] ^ (st[3] >> 3);",
+     "uint32_t t5 = st[2] ^ (st[2] >> 3);", pv.check_xorshift8_lags),
+    ("r=8 XorShift drops R^7", "uint32_t t8 = st[0] ^ (st[0] >> 7);", "uint32_t t8 = st[0];",
+     pv.check_xorshift8_full_period),
+    ("two-part MWC joined with or", "(((uint64_t)st[0] << 16) + st[1])",
+     "(((uint64_t)st[0] << 16) | (st[1] & 0xFFFFu))", pv.check_mwc16x2_closed_form),
+    ("two-part MWC parts swapped", "uint32_t a1 = a_pair & 0xFFFFu, a2 = a_pair >> 16;\n    uint32_t x = st[0]",
+     "uint32_t a2 = a_pair & 0xFFFFu, a1 = a_pair >> 16;\n    uint32_t x = st[0]",
+     pv.check_mwc16x2_closed_form),
+    ("paper KISS in the sum form", "((uint64_t)(m ^ z) + y)", "((uint64_t)m + z + y)",
+     pv.check_kiss_xor_is_parts),
+    ("multiplier pairs reversed", "out[found++] = table[i] | (table[j] << 16);",
+     "out[found++] = table[j] | (table[i] << 16);", pv.check_mwc16_pairs_lexicographic),
 ]
 
 
