@@ -18,6 +18,20 @@
  *              step y ^= y<<13; y ^= y>>17; y ^= y<<5 (Eq. 6) and one LCG
  *              step z = 69069 z + 1234567 mod 2^32 (Eq. 7); out is the sum
  *              of the three new values mod 2^32.
+ *   The paper's own generators:
+ *   RNG_MWC16X2  two base-2^16 MWCs (Methods / MWC), each kept as one word
+ *              z = x + c 2^16 and stepped as z' = a (z & 0xFFFF) + (z >> 16);
+ *              out = (z' << 16) + w' mod 2^32.  Stream s has the s-th pair
+ *              (i < j, lexicographic) of the 392 multipliers a < 2^16 with
+ *              a 2^16 - 1 a safe prime (largest first): a1 = table[i] for z,
+ *              a2 = table[j] for w.
+ *   RNG_XORSHIFT8  Panneton's r = 8, s = 7 XorShift (Eq. 5): words
+ *              (v_{n-8} .. v_{n-1}); v_n = (I+L^9)(I+L^13) v_{n-1} +
+ *              (I+L^7) v_{n-4} + (I+R^3) v_{n-5} + (I+R^10) v_{n-7} +
+ *              (I+L^24)(I+R^7) v_{n-8} (xor; products applied right to left);
+ *              out = v_n.
+ *   RNG_KISS_XOR  KISS in the paper's form: ((MWC16X2 xor LCG) + xorshift32)
+ *              mod 2^32, with the MWC pair, Eq. 6 and Eq. 7 as above.
  * Formats (fmt):
  *   RNG_U32    the 32-bit output.
  *   RNG_F32    (float)(u >> 8) * 2^-24, exactly; in [0, 1 - 2^-24]
@@ -28,7 +42,11 @@
  * of a draw, redrawn while (x, c) is (0, 0) or (2^32 - 1, a - 1); xor128
  * words = lo32, hi32 of two draws, redrawn while all zero; KISS (x, c) as
  * MWC, then y = lo32 and z = hi32 of the next draw, y redrawn (lo32 of
- * further draws) while zero.
+ * further draws) while zero.  MWC16X2: from one draw r, part 1 x = bits
+ * 0-15, c = bits 16-31 mod a1, part 2 x = bits 32-47, c = bits 48-63 mod a2,
+ * redrawn while either part is a fixed point; XORSHIFT8: the eight words are
+ * lo32, hi32 of four draws, redrawn while all zero; KISS_XOR: the MWC pair as
+ * MWC16X2, then y and the LCG word as KISS.
  *
  * Output layout (stream-interleaved): output j (0-based, counted from the
  * start of the call) of stream s is element out[j * n_streams + s].  Each
@@ -63,7 +81,14 @@ extern "C" {
 
 typedef struct rng_gen *rng_handle;
 
-enum rng_kind { RNG_MWC32 = 0, RNG_XOR128 = 1, RNG_KISS = 2 };
+enum rng_kind {
+    RNG_MWC32 = 0,
+    RNG_XOR128 = 1,
+    RNG_KISS = 2,
+    RNG_MWC16X2 = 3,
+    RNG_XORSHIFT8 = 4,
+    RNG_KISS_XOR = 5
+};
 enum rng_fmt { RNG_U32 = 0, RNG_F32 = 1 };
 
 enum rng_status {
@@ -82,6 +107,11 @@ enum rng_status {
 #define RNG_MAX_STREAMS_MWC ((uint64_t)1 << 22)
 /* Largest stream count of an xor128 generator (no multiplier table). */
 #define RNG_MAX_STREAMS_XOR ((uint64_t)1 << 30)
+/* Largest stream count of an MWC16X2 or KISS_XOR generator: the number of
+ * distinct pairs of the 392 base-2^16 multipliers. */
+#define RNG_MAX_STREAMS_MWC16 ((uint64_t)392 * 391 / 2)
+/* Largest stream count of an XORSHIFT8 generator (8 GiB of state). */
+#define RNG_MAX_STREAMS_XS8 ((uint64_t)1 << 28)
 
 /* Creates a generator of `kind` with n_streams independent streams seeded
  * from `seed` (header comment).  Allocates the per-stream state (and, for
@@ -103,8 +133,8 @@ void rng_destroy(rng_handle h);
  * and must not destroy it while work of the handle is pending. */
 int rng_set_stream(rng_handle h, void *cuda_stream);
 
-/* Number of streams and of 32-bit state words per stream (2 for MWC32,
- * 4 for xor128 and KISS). */
+/* Number of streams and of 32-bit state words per stream (2 for MWC32 and
+ * MWC16X2, 8 for XORSHIFT8, 4 for the others). */
 uint64_t rng_n_streams(rng_handle h);
 int rng_state_words(rng_handle h);
 
@@ -231,6 +261,13 @@ int rng_get_device_view(rng_handle h, rng_device_view *view);
  * Paper: the multiplier condition of the background MWC section. */
 int rng_multipliers(uint64_t k, uint32_t *dev_out);
 
+/* Writes the first k multiplier pairs of MWC16X2 / KISS_XOR streams, packed
+ * a1 | a2 << 16, to `dev_out` (DEVICE, caller-owned, k uint32); k <=
+ * RNG_MAX_STREAMS_MWC16.  Builds the 392-entry base-2^16 table on the
+ * current device on first use; SYNCHRONISES the device.
+ * Paper: pairs of the 392 multipliers, one pair per thread (Methods / MWC). */
+int rng_mwc16_pairs(uint64_t k, uint32_t *dev_out);
+
 /* One entry of a batched launch: generator h advances streams
  * [s_begin, s_end) n_per_stream times and writes output j of stream s to
  * out[j * ld + (s - s_begin)] (DEVICE pointer, 4-byte aligned) in format
@@ -258,9 +295,12 @@ typedef struct rng_plan *rng_plan_handle;
  * 0 = as many as fit).  Items of the same handle must cover disjoint stream
  * ranges (they then run side by side); items with n_per_stream = 0 are
  * skipped.  The plan refers to the handles' device
- * memory and the out pointers: it must not outlive them.  Returns NULL with
- * rng_last_error() = RNG_ERR_ARG (bad item, duplicate handle, handles on
- * different devices, n_per_stream >= 2^32), RNG_ERR_OOM or RNG_ERR_CUDA.
+ * memory and the out pointers: it must not outlive them.  Items must be
+ * of the kinds RNG_MWC32, RNG_XOR128 or RNG_KISS (the persistent kernel
+ * carries the bodies of those three only, so that the paper's larger-state
+ * variants do not cost the common case registers).  Returns NULL with
+ * rng_last_error() = RNG_ERR_ARG (bad item or kind, duplicate handle, handles
+ * on different devices, n_per_stream >= 2^32), RNG_ERR_OOM or RNG_ERR_CUDA.
  * Paper: none; the parametrised streams of Sec. "Parallelizing RNGs" served
  * as one launch. */
 rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n_items,
@@ -326,8 +366,9 @@ int rng_generate_batch(const rng_batch_item *items, size_t n_items,
  * ------------------------------------------------------------------- */
 typedef struct rng_server *rng_server_handle;
 
-/* kind: any generator kind; n_clients >= 1; streams_per_client within the
- * kind's maximum; budget_bytes: device memory for state plus outputs;
+/* kind: RNG_MWC32, RNG_XOR128 or RNG_KISS (the engine batches through the
+ * persistent kernel of rng_plan_create); n_clients >= 1; streams_per_client
+ * within the kind's maximum; budget_bytes: device memory for state plus outputs;
  * chunk_rows >= 1.  Allocates everything up front (synchronises).  NULL on
  * failure (rng_last_error(): RNG_ERR_ARG, RNG_ERR_OOM when the budget does
  * not cover the state, RNG_ERR_CUDA, RNG_ERR_NODEV). */

@@ -12,15 +12,19 @@ from pathlib import Path
 LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libgbrng.so"
 
 RNG_MWC32, RNG_XOR128, RNG_KISS = 0, 1, 2
+RNG_MWC16X2, RNG_XORSHIFT8, RNG_KISS_XOR = 3, 4, 5
 RNG_U32, RNG_F32 = 0, 1
 RNG_OK, RNG_ERR_ARG, RNG_ERR_OOM, RNG_ERR_CUDA = 0, -1, -2, -3
 RNG_ERR_TIMEOUT, RNG_ERR_BUSY, RNG_ERR_NODEV = -4, -5, -6
 RNG_MAX_STREAMS_MWC = 1 << 22
 RNG_MAX_STREAMS_XOR = 1 << 30
+RNG_MAX_STREAMS_MWC16 = 392 * 391 // 2
+RNG_MAX_STREAMS_XS8 = 1 << 28
 
 RNG_SUM_U32, RNG_SUM_U24, RNG_DISC = 0, 1, 2
 
-KINDS = {"mwc": RNG_MWC32, "xor128": RNG_XOR128, "kiss": RNG_KISS}
+KINDS = {"mwc": RNG_MWC32, "xor128": RNG_XOR128, "kiss": RNG_KISS, "mwc16x2": RNG_MWC16X2,
+         "xorshift8": RNG_XORSHIFT8, "kiss_xor": RNG_KISS_XOR}
 FMTS = {"u32": RNG_U32, "f32": RNG_F32}
 
 
@@ -54,6 +58,7 @@ SIGNATURES = {
     "rng_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "rng_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "rng_multipliers": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p]),
+    "rng_mwc16_pairs": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_void_p]),
     "rng_generate_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                            ctypes.c_void_p]),
     "rng_jump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),

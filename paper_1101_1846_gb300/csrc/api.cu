@@ -41,12 +41,18 @@ bool device_supported(int dev)
     return prop.major == 10 && prop.minor == 3;
 }
 
-bool valid_kind(int k) { return k == RNG_MWC32 || k == RNG_XOR128 || k == RNG_KISS; }
+bool valid_kind(int k) { return k >= 0 && k < kKinds; }
 bool valid_fmt(int f) { return f == RNG_U32 || f == RNG_F32; }
 
 uint64_t max_streams(int kind)
 {
-    return kind == RNG_XOR128 ? RNG_MAX_STREAMS_XOR : RNG_MAX_STREAMS_MWC;
+    switch (kind) {
+    case RNG_XOR128: return RNG_MAX_STREAMS_XOR;
+    case RNG_MWC16X2:
+    case RNG_KISS_XOR: return RNG_MAX_STREAMS_MWC16;
+    case RNG_XORSHIFT8: return RNG_MAX_STREAMS_XS8;
+    default: return RNG_MAX_STREAMS_MWC;
+    }
 }
 
 void free_gen(Gen *g)
@@ -115,9 +121,11 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     int st = RNG_OK;
     if (cudaMalloc(&g->d_state, (size_t)g->words * n_streams * 4) != cudaSuccess) {
         st = set_error(RNG_ERR_OOM);
-    } else if (kind != RNG_XOR128) {
+    } else if (has_mult(kind)) {
+        // one multiplier per stream, or one packed pair for the base-2^16 kinds
         const uint32_t *table = nullptr;
-        st = multiplier_table(n_streams, &table);
+        st = kind == RNG_MWC16X2 || kind == RNG_KISS_XOR ? mwc16_pair_table(n_streams, &table)
+                                                         : multiplier_table(n_streams, &table);
         if (!st && cudaMalloc(&g->d_a, n_streams * 4) != cudaSuccess)
             st = set_error(RNG_ERR_OOM);
         if (!st)
@@ -129,7 +137,7 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
         g->jmul_segs = split_max_segments(n_streams);
         if (cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess ||
             cudaMalloc(&g->d_cnt, n_streams * 4) != cudaSuccess ||
-            (kind != RNG_XOR128 &&
+            (mont_table(kind) &&
              cudaMalloc(&g->d_jmul, (size_t)g->jmul_segs * n_streams * 8) != cudaSuccess))
             st = set_error(RNG_ERR_OOM);
         else
@@ -138,7 +146,7 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     // jump tables of the xorshift and LCG parts, built here so that no later
     // call (which may be captured in a CUDA graph) has to build them
     JumpTables tables;
-    if (!st && kind != RNG_MWC32)
+    if (!st && needs_jump_tables(kind))
         st = jump_tables(&tables);
     if (!st)
         st = launch_seed(g, nullptr);
@@ -336,10 +344,29 @@ extern "C" int rng_set_state(rng_handle h, const void *host_buf, size_t bytes)
     DeviceGuard dg(g->device);
     const uint32_t *w = static_cast<const uint32_t *>(host_buf);
     const uint64_t n = g->n;
-    if (g->kind == RNG_XOR128) {
-        for (uint64_t s = 0; s < n; ++s)
-            if ((w[s] | w[n + s] | w[2 * n + s] | w[3 * n + s]) == 0)
+    if (g->kind == RNG_XOR128 || g->kind == RNG_XORSHIFT8) {
+        for (uint64_t s = 0; s < n; ++s) {
+            uint32_t any = 0;
+            for (int k = 0; k < g->words; ++k)
+                any |= w[k * n + s];
+            if (any == 0)
                 return set_error(RNG_ERR_ARG);
+        }
+    } else if (g->kind == RNG_MWC16X2 || g->kind == RNG_KISS_XOR) {
+        std::vector<uint32_t> a(n);
+        int st = cuda_status(cudaMemcpy(a.data(), g->d_a, n * 4, cudaMemcpyDeviceToHost));
+        if (st)
+            return st;
+        for (uint64_t s = 0; s < n; ++s) {
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t ap = part ? a[s] >> 16 : a[s] & 0xFFFFu;
+                const uint32_t z = w[part * n + s], x = z & 0xFFFFu, c = z >> 16;
+                if (c >= ap || (x == 0 && c == 0) || (x == 0xFFFFu && c == ap - 1))
+                    return set_error(RNG_ERR_ARG);
+            }
+            if (g->kind == RNG_KISS_XOR && w[2 * n + s] == 0)
+                return set_error(RNG_ERR_ARG);
+        }
     } else {
         std::vector<uint32_t> a(n);
         int st = cuda_status(cudaMemcpy(a.data(), g->d_a, n * 4, cudaMemcpyDeviceToHost));

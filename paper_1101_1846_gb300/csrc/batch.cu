@@ -116,7 +116,8 @@ int validate_items(const rng_batch_item *items, size_t n_items, Claim *scratch, 
     for (size_t i = 0; i < n_items; ++i) {
         const rng_batch_item &it = items[i];
         Gen *g = reinterpret_cast<Gen *>(it.h);
-        if (!g || (it.fmt != RNG_U32 && it.fmt != RNG_F32))
+        if (!g || (it.fmt != RNG_U32 && it.fmt != RNG_F32) ||
+            (g->kind != RNG_MWC32 && g->kind != RNG_XOR128 && g->kind != RNG_KISS))
             return set_error(RNG_ERR_ARG);
         if (*device < 0)
             *device = g->device;

@@ -57,12 +57,26 @@ int cuda_status(cudaError_t e);
 
 // multipliers.cu: makes the device table at least k long; returns its base.
 int multiplier_table(uint64_t k, const uint32_t **table);
+// The packed base-2^16 multiplier pairs of MWC16X2 / KISS_XOR streams (all
+// RNG_MAX_STREAMS_MWC16 of them, built once per device; synchronises then).
+int mwc16_pair_table(uint64_t k, const uint32_t **pairs);
 
 // seed.cu
 int launch_seed(Gen *g, cudaStream_t st);
 
-// generate.cu
+constexpr int kKinds = 6;
+
+// generate.cu: the launch shape of the vector kernels per (kind, fmt)
+// (gbrng_set_launch), and one generate call of any kind.
+struct LaunchShape {
+    int v;      // groups of four streams per thread
+    int block;  // CTA size
+    int hint;   // streaming stores
+};
+LaunchShape launch_shape(int kind, int fmt);
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st);
+// generate_paper.cu: the same for RNG_MWC16X2, RNG_XORSHIFT8, RNG_KISS_XOR.
+int launch_generate_paper(int kind, int fmt, const GenLaunch &p, cudaStream_t st);
 // Segments of a split call: rows per segment (a power of two) and count
 // (at most max_segments); returns false when the call should run unsplit.
 // `streams` are the streams the call advances, `streams_per_thread` how many
@@ -76,6 +90,8 @@ struct JumpTables {
     const uint4 *xor128;      // [m][j]: column j of M^(2^m), M = one xor128 step
     const uint32_t *xs32;     // [m][j]: column j of X^(2^m), X = one xorshift32 step
     const uint2 *lcg;         // [m]: (A, C) of the LCG map applied 2^m times
+    const uint4 *xs8;         // [m][2j], [m][2j+1]: column j of Y^(2^m), Y = one
+                              // XORSHIFT8 step (words 0-3, 4-7)
 };
 int jump_tables(JumpTables *t);
 int launch_jump(Gen *g, uint64_t k, cudaStream_t st);
@@ -85,7 +101,15 @@ int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **tabl
 // Most segments a split call on a handle of n streams can have.
 uint32_t split_max_segments(uint64_t n);
 
-inline int words_of(int kind) { return kind == RNG_MWC32 ? 2 : 4; }
+inline int words_of(int kind)
+{
+    return kind == RNG_MWC32 || kind == RNG_MWC16X2 ? 2 : kind == RNG_XORSHIFT8 ? 8 : 4;
+}
+inline bool has_mult(int kind) { return kind != RNG_XOR128 && kind != RNG_XORSHIFT8; }
+// Kinds whose split jumps use the handle's table of Montgomery powers.
+inline bool mont_table(int kind) { return kind == RNG_MWC32 || kind == RNG_KISS; }
+// Kinds that need the device jump tables (GF(2) or affine parts).
+inline bool needs_jump_tables(int kind) { return kind != RNG_MWC32 && kind != RNG_MWC16X2; }
 
 // Handles with at most this many streams keep a split scratch (split calls
 // only happen for stream counts well below it).

@@ -20,26 +20,46 @@
 
 namespace gbrng {
 
+// Per kind: state words per stream (W) and whether each stream has a
+// multiplier word (MULT: a multiplier, or a packed pair of 16-bit ones).
 template <int KIND>
-struct Words;
+struct KindTraits;
 template <>
-struct Words<RNG_MWC32> { static constexpr int W = 2; };
+struct KindTraits<RNG_MWC32> { static constexpr int W = 2; static constexpr bool MULT = true; };
 template <>
-struct Words<RNG_XOR128> { static constexpr int W = 4; };
+struct KindTraits<RNG_XOR128> { static constexpr int W = 4; static constexpr bool MULT = false; };
 template <>
-struct Words<RNG_KISS> { static constexpr int W = 4; };
+struct KindTraits<RNG_KISS> { static constexpr int W = 4; static constexpr bool MULT = true; };
+template <>
+struct KindTraits<RNG_MWC16X2> { static constexpr int W = 2; static constexpr bool MULT = true; };
+template <>
+struct KindTraits<RNG_XORSHIFT8> { static constexpr int W = 8; static constexpr bool MULT = false; };
+template <>
+struct KindTraits<RNG_KISS_XOR> { static constexpr int W = 4; static constexpr bool MULT = true; };
+
+// Register arrays hold up to kMaxWords words per stream; a kind touches only
+// its first W, and the unused entries cost no registers.
+constexpr int kMaxWords = 8;
 
 // One step of stream i of a group of four: w[word][i], a[i].
 template <int KIND, int FMT>
-__device__ __forceinline__ uint32_t step_enc(uint32_t (&w)[4][4], const uint32_t (&a)[4], int i)
+__device__ __forceinline__ uint32_t step_enc(uint32_t (&w)[kMaxWords][4],
+                                             const uint32_t (&a)[4], int i)
 {
     uint32_t u;
     if constexpr (KIND == RNG_MWC32)
         u = mwc_step(a[i], w[0][i], w[1][i]);
     else if constexpr (KIND == RNG_XOR128)
         u = xor128_step(w[0][i], w[1][i], w[2][i], w[3][i]);
-    else
+    else if constexpr (KIND == RNG_KISS)
         u = kiss_step(a[i], w[0][i], w[1][i], w[2][i], w[3][i]);
+    else if constexpr (KIND == RNG_MWC16X2)
+        u = mwc16x2_step(a[i], w[0][i], w[1][i]);
+    else if constexpr (KIND == RNG_XORSHIFT8)
+        u = xorshift8_step(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i], w[5][i], w[6][i],
+                           w[7][i]);
+    else
+        u = kiss_xor_step(a[i], w[0][i], w[1][i], w[2][i], w[3][i]);
     if constexpr (FMT == RNG_F32)
         return __float_as_uint(unit_f32(u));
     else
@@ -91,8 +111,8 @@ __device__ __forceinline__ void body_vec(uint32_t *__restrict__ state,
                                          uint32_t steps, uint32_t *__restrict__ row0,
                                          uint64_t ld, uint64_t s_first, uint64_t v_stride)
 {
-    constexpr int W = Words<KIND>::W;
-    uint32_t w[V][4][4];
+    constexpr int W = KindTraits<KIND>::W;
+    uint32_t w[V][kMaxWords][4];
     uint32_t a[V][4];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -100,7 +120,7 @@ __device__ __forceinline__ void body_vec(uint32_t *__restrict__ state,
 #pragma unroll
         for (int k = 0; k < W; ++k)
             load4(state + k * n + s0, w[v][k]);
-        if constexpr (KIND != RNG_XOR128)
+        if constexpr (KindTraits<KIND>::MULT)
             load4(mult + s0, a[v]);
         else
             a[v][0] = a[v][1] = a[v][2] = a[v][3] = 0;
@@ -141,14 +161,14 @@ __device__ __forceinline__ void body_vec_sync(uint32_t *__restrict__ state,
                                               uint32_t steps, uint32_t *__restrict__ row0,
                                               uint64_t ld, uint64_t s_first, bool live)
 {
-    constexpr int W = Words<KIND>::W;
-    uint32_t w[4][4] = {};
+    constexpr int W = KindTraits<KIND>::W;
+    uint32_t w[kMaxWords][4] = {};
     uint32_t a[4] = {0, 0, 0, 0};
     if (live) {
 #pragma unroll
         for (int k = 0; k < W; ++k)
             load4(state + k * n + s_first, w[k]);
-        if constexpr (KIND != RNG_XOR128)
+        if constexpr (KindTraits<KIND>::MULT)
             load4(mult + s_first, a);
     }
     uint32_t *row = row0;
@@ -195,7 +215,7 @@ __device__ __forceinline__ void body_vec_sync(uint32_t *__restrict__ state,
 // EDGE warps also store the stray words singly: the CTA's first lane its
 // words 0 .. 3-R, the owner of its last group its words 4-R .. 3.
 template <int KIND, int FMT, int HINT, int R, bool EDGE>
-__device__ __forceinline__ void shift_row(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+__device__ __forceinline__ void shift_row(uint32_t (&w)[kMaxWords][4], const uint32_t (&a)[4],
                                           uint32_t *row, bool owner, bool prev, bool next,
                                           bool lead, bool trail)
 {
@@ -243,7 +263,7 @@ __device__ __forceinline__ void shift_row(uint32_t (&w)[4][4], const uint32_t (&
 // Rows in blocks of four: the alignment of row j + 4 equals that of row j,
 // so within a block every row's alignment is a compile-time constant.
 template <int KIND, int FMT, int HINT, int R0, int DR, bool EDGE>
-__device__ __forceinline__ void shift_rows(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+__device__ __forceinline__ void shift_rows(uint32_t (&w)[kMaxWords][4], const uint32_t (&a)[4],
                                            uint32_t *&row, uint64_t ld, uint32_t blocks,
                                            bool owner, bool prev, bool next, bool lead,
                                            bool trail)
@@ -265,7 +285,7 @@ __device__ __forceinline__ void shift_rows(uint32_t (&w)[4][4], const uint32_t (
 }
 
 template <int KIND, int FMT, int HINT, bool EDGE>
-__device__ __forceinline__ void shift_rows_dispatch(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+__device__ __forceinline__ void shift_rows_dispatch(uint32_t (&w)[kMaxWords][4], const uint32_t (&a)[4],
                                                     uint32_t *&row, uint64_t ld, uint32_t r0,
                                                     uint32_t blocks, bool owner, bool prev,
                                                     bool next, bool lead, bool trail)
@@ -289,7 +309,7 @@ __device__ __forceinline__ void shift_rows_dispatch(uint32_t (&w)[4][4], const u
 // One row with a run-time alignment (the at most three rows after the
 // blocks of four).
 template <int KIND, int FMT, int HINT>
-__device__ __forceinline__ void shift_row_rt(uint32_t (&w)[4][4], const uint32_t (&a)[4],
+__device__ __forceinline__ void shift_row_rt(uint32_t (&w)[kMaxWords][4], const uint32_t (&a)[4],
                                              uint32_t *row, uint32_t r, bool owner, bool prev,
                                              bool next, bool lead, bool trail)
 {
@@ -321,7 +341,7 @@ __device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,
                                            uint32_t steps, uint32_t *__restrict__ cta_row0,
                                            uint64_t ld, uint64_t cta_s0, uint32_t groups)
 {
-    constexpr int W = Words<KIND>::W;
+    constexpr int W = KindTraits<KIND>::W;
     const int lane = threadIdx.x & 31;
     const int k = threadIdx.x >> 5;
     const int K = blockDim.x >> 5;
@@ -333,13 +353,13 @@ __device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,
     const bool prev = live && lane > 0;                              // chunk C
     const bool next = owner && lane < 31 && g + 1 < groups;          // chunk C + 4
     const uint64_t s_first = cta_s0 + 4 * (uint64_t)g;
-    uint32_t w[4][4];
+    uint32_t w[kMaxWords][4];
     uint32_t a[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         a[i] = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < kMaxWords; ++q)
             w[q][i] = 0;
     }
     if (live) {
@@ -348,7 +368,7 @@ __device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,
 #pragma unroll
             for (int q = 0; q < W; ++q)
                 w[q][i] = state[q * n + s_first + i];
-            if constexpr (KIND != RNG_XOR128)
+            if constexpr (KindTraits<KIND>::MULT)
                 a[i] = mult[s_first + i];
         }
     }
@@ -388,13 +408,13 @@ __device__ __forceinline__ void body_scalar(uint32_t *__restrict__ state,
                                             uint32_t steps, uint32_t *__restrict__ p0,
                                             uint64_t ld, uint64_t s)
 {
-    constexpr int W = Words<KIND>::W;
-    uint32_t w[4][4];
+    constexpr int W = KindTraits<KIND>::W;
+    uint32_t w[kMaxWords][4];
     uint32_t a[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kMaxWords; ++k)
         w[k][0] = k < W ? state[k * n + s] : 0;
-    if constexpr (KIND != RNG_XOR128)
+    if constexpr (KindTraits<KIND>::MULT)
         a[0] = mult[s];
     uint32_t *p = p0;
 #pragma unroll 4

@@ -248,6 +248,107 @@ int upload_primes()
     return cuda_status(cudaMemcpyToSymbol(c_primes, &h, sizeof(h)));
 }
 
+// ------------------------------------------------ base-2^16 multipliers
+// The paper's two-part MWC uses multipliers a < 2^16 with p = a 2^16 - 1 and
+// q = a 2^15 - 1 both prime (392 of them).  p < 2^32, so Miller-Rabin with
+// the bases 2, 7 and 61 is exact (no composite below 4,759,123,141 passes
+// all three; Jaeschke 1993).  p, q >= 32767 > 61.
+__device__ bool is_prime_u32(uint32_t n)
+{
+    if (n % 2 == 0)
+        return n == 2;
+    uint32_t d = n - 1;
+    int r = 0;
+    while ((d & 1) == 0) {
+        d >>= 1;
+        ++r;
+    }
+    const uint32_t bases[3] = {2, 7, 61};
+    for (int i = 0; i < 3; ++i) {
+        uint64_t x = 1, b = bases[i] % n;
+        for (uint32_t e = d; e; e >>= 1) {
+            if (e & 1)
+                x = x * b % n;
+            b = b * b % n;
+        }
+        if (x == 1 || x == n - 1)
+            continue;
+        bool composite = true;
+        for (int k = 1; k < r; ++k) {
+            x = x * x % n;
+            if (x == n - 1) {
+                composite = false;
+                break;
+            }
+        }
+        if (composite)
+            return false;
+    }
+    return true;
+}
+
+// One CTA of 1024 threads: thread t tests a = 65535 - 64 t - i, i < 64
+// (descending), and an exclusive scan of the hit counts in thread order puts
+// the hits in descending order.
+__global__ void __launch_bounds__(1024) mwc16_table_kernel(uint32_t *table, uint32_t *count)
+{
+    __shared__ uint32_t warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint64_t hits = 0;  // bit i: a = 65535 - 64 t - i passes
+    for (int i = 0; i < 64; ++i) {
+        const uint32_t a = 65535u - 64u * t - i;
+        if (a >= 1 && is_prime_u32((a << 15) - 1) && is_prime_u32((a << 16) - 1))
+            hits |= 1ull << i;
+    }
+    const uint32_t c = __popcll(hits);
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += v;
+    }
+    if (lane == 31)
+        warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sum[lane], wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += v;
+        }
+        warp_sum[lane] = wi - w;  // exclusive
+        if (lane == 31)
+            *count = wi;
+    }
+    __syncthreads();
+    uint32_t pos = warp_sum[warp] + incl - c;
+    for (int i = 0; i < 64; ++i)
+        if ((hits >> i) & 1)
+            table[pos++] = 65535u - 64u * t - i;
+}
+
+// Pair s (lexicographic, i < j) of the m-entry table, packed table[i] |
+// table[j] << 16.
+__global__ void mwc16_pairs_kernel(const uint32_t *table, uint32_t m, uint64_t k, uint32_t *out)
+{
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k)
+        return;
+    uint64_t r = s;
+    uint32_t i = 0;
+    while (i + 1 < m && r >= m - 1 - i) {
+        r -= m - 1 - i;
+        ++i;
+    }
+    out[s] = table[i] | (table[i + 1 + r] << 16);
+}
+
+struct DevicePairs {
+    uint32_t *pairs = nullptr;  // all 392 * 391 / 2 pairs
+};
+DevicePairs g_pairs[64];
+
 }  // namespace
 
 int multiplier_table(uint64_t k, const uint32_t **out)
@@ -355,6 +456,66 @@ int multiplier_table(uint64_t k, const uint32_t **out)
 }
 
 }  // namespace gbrng
+
+namespace gbrng {
+
+int mwc16_pair_table(uint64_t k, const uint32_t **out)
+{
+    if (k == 0 || k > RNG_MAX_STREAMS_MWC16)
+        return set_error(RNG_ERR_ARG);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return set_error(RNG_ERR_NODEV);
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DevicePairs &P = g_pairs[dev];
+    if (!P.pairs) {
+        uint32_t *table = nullptr, *count = nullptr, *pairs = nullptr;
+        int st = RNG_OK;
+        if (cudaMalloc(&table, 1024 * 4) != cudaSuccess || cudaMalloc(&count, 4) != cudaSuccess ||
+            cudaMalloc(&pairs, RNG_MAX_STREAMS_MWC16 * 4) != cudaSuccess)
+            st = set_error(RNG_ERR_OOM);
+        uint32_t m = 0;
+        if (!st) {
+            mwc16_table_kernel<<<1, 1024>>>(table, count);
+            st = cuda_status(cudaGetLastError());
+        }
+        if (!st)
+            st = cuda_status(cudaMemcpy(&m, count, 4, cudaMemcpyDeviceToHost));
+        if (!st && (uint64_t)m * (m - 1) / 2 != RNG_MAX_STREAMS_MWC16)
+            st = set_error(RNG_ERR_CUDA);  // the search must find exactly 392
+        if (!st) {
+            const uint64_t total = RNG_MAX_STREAMS_MWC16;
+            mwc16_pairs_kernel<<<(unsigned)((total + 255) / 256), 256>>>(table, m, total, pairs);
+            st = cuda_status(cudaGetLastError());
+        }
+        if (!st)
+            st = cuda_status(cudaDeviceSynchronize());
+        cudaFree(table);
+        cudaFree(count);
+        if (st) {
+            cudaFree(pairs);
+            return st;
+        }
+        P.pairs = pairs;
+    }
+    *out = P.pairs;
+    return RNG_OK;
+}
+
+}  // namespace gbrng
+
+extern "C" int rng_mwc16_pairs(uint64_t k, uint32_t *dev_out)
+{
+    using namespace gbrng;
+    if (!dev_out || k == 0 || k > RNG_MAX_STREAMS_MWC16)
+        return set_error(RNG_ERR_ARG);
+    const uint32_t *t = nullptr;
+    int st = mwc16_pair_table(k, &t);
+    if (st)
+        return st;
+    cudaError_t e = cudaMemcpy(dev_out, t, k * 4, cudaMemcpyDeviceToDevice);
+    return e == cudaSuccess ? RNG_OK : cuda_status(e);
+}
 
 extern "C" int rng_multipliers(uint64_t k, uint32_t *dev_out)
 {

@@ -76,7 +76,8 @@ reduce_kernel(rng_device_view v, uint64_t steps, uint64_t rows, uint64_t *__rest
     }
     const uint64_t first = (uint64_t)blockIdx.y * rows;
     const uint64_t mine = steps - first < rows ? steps - first : rows;
-    const uint64_t A = (KIND != RNG_XOR128 && blockIdx.y > 0) ? jmul[blockIdx.y * n + s] : 0;
+    const uint64_t A =
+        ((KIND == RNG_MWC32 || KIND == RNG_KISS) && blockIdx.y > 0) ? jmul[blockIdx.y * n + s] : 0;
     jump_engine<KIND>(e, first, T, A);
     atomicAdd(reinterpret_cast<unsigned long long *>(out + s),
               (unsigned long long)consume<OP>(e, mine));
@@ -108,9 +109,14 @@ ReduceFn pick(int op)
 template <bool SPLIT>
 ReduceFn pick_kind(int kind, int op)
 {
-    return kind == RNG_MWC32    ? pick<RNG_MWC32, SPLIT>(op)
-           : kind == RNG_XOR128 ? pick<RNG_XOR128, SPLIT>(op)
-                                : pick<RNG_KISS, SPLIT>(op);
+    switch (kind) {
+    case RNG_MWC32: return pick<RNG_MWC32, SPLIT>(op);
+    case RNG_XOR128: return pick<RNG_XOR128, SPLIT>(op);
+    case RNG_KISS: return pick<RNG_KISS, SPLIT>(op);
+    case RNG_MWC16X2: return pick<RNG_MWC16X2, SPLIT>(op);
+    case RNG_XORSHIFT8: return pick<RNG_XORSHIFT8, SPLIT>(op);
+    default: return pick<RNG_KISS_XOR, SPLIT>(op);
+    }
 }
 
 }  // namespace
@@ -143,9 +149,9 @@ extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, 
     JumpTables T{};
     const uint64_t *jmul = nullptr;
     int status = RNG_OK;
-    if (split && g->kind != RNG_MWC32)
+    if (split && needs_jump_tables(g->kind))
         status = jump_tables(&T);
-    if (!status && split && g->kind != RNG_XOR128)
+    if (!status && split && mont_table(g->kind))
         status = mwc_jump_table(g, rows, st, &jmul);
     if (!status && split)
         status = cuda_status(cudaMemsetAsync(o, 0, g->n * 8, st));

@@ -7,6 +7,11 @@
 //   xor128 (x, y, z, w) = lo/hi of two draws; redraw both while all zero
 //   KISS   (x, c) as MWC32; then y = lo32, z = hi32 of the next draw; y
 //          replaced by lo32 of further draws while zero
+//   MWC16X2  from one draw r: part 1 x = bits 0-15, c = bits 16-31 mod a1,
+//          part 2 x = bits 32-47, c = bits 48-63 mod a2, each kept as
+//          x | c << 16; redraw while either part is a fixed point
+//   XORSHIFT8  eight words = lo32, hi32 of four draws; redraw while all zero
+//   KISS_XOR  the pair as MWC16X2, then y and the LCG word as KISS
 #include "gbrng.cuh"
 
 namespace gbrng {
@@ -34,6 +39,24 @@ __device__ __forceinline__ void draw_mwc(uint64_t &z, uint32_t a, uint32_t &x, u
     }
 }
 
+__device__ __forceinline__ void draw_mwc16x2(uint64_t &z, uint32_t a_pair, uint32_t &p1,
+                                             uint32_t &p2)
+{
+    const uint32_t a1 = a_pair & 0xFFFFu, a2 = a_pair >> 16;
+    for (;;) {
+        const uint64_t r = splitmix64_next(z);
+        const uint32_t x1 = (uint32_t)(r & 0xFFFFu), c1 = (uint32_t)((r >> 16) & 0xFFFFu) % a1;
+        const uint32_t x2 = (uint32_t)((r >> 32) & 0xFFFFu), c2 = (uint32_t)(r >> 48) % a2;
+        const bool bad1 = (x1 == 0 && c1 == 0) || (x1 == 0xFFFFu && c1 == a1 - 1);
+        const bool bad2 = (x2 == 0 && c2 == 0) || (x2 == 0xFFFFu && c2 == a2 - 1);
+        if (!bad1 && !bad2) {
+            p1 = x1 | (c1 << 16);
+            p2 = x2 | (c2 << 16);
+            return;
+        }
+    }
+}
+
 __global__ void seed_kernel(int kind, uint64_t n, uint64_t seed, const uint32_t *a,
                             uint32_t *state)
 {
@@ -41,6 +64,40 @@ __global__ void seed_kernel(int kind, uint64_t n, uint64_t seed, const uint32_t 
     if (s >= n)
         return;
     uint64_t z = seed + s;
+    if (kind == RNG_MWC16X2 || kind == RNG_KISS_XOR) {
+        uint32_t p1, p2;
+        draw_mwc16x2(z, a[s], p1, p2);
+        state[s] = p1;
+        state[n + s] = p2;
+        if (kind == RNG_KISS_XOR) {
+            const uint64_t r = splitmix64_next(z);
+            uint32_t y = (uint32_t)r;
+            const uint32_t l = (uint32_t)(r >> 32);
+            while (y == 0)
+                y = (uint32_t)splitmix64_next(z);
+            state[2 * n + s] = y;
+            state[3 * n + s] = l;
+        }
+        return;
+    }
+    if (kind == RNG_XORSHIFT8) {
+        uint32_t v[8];
+        uint32_t any;
+        do {
+            any = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t r = splitmix64_next(z);
+                v[2 * i] = (uint32_t)r;
+                v[2 * i + 1] = (uint32_t)(r >> 32);
+                any |= v[2 * i] | v[2 * i + 1];
+            }
+        } while (any == 0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            state[k * n + s] = v[k];
+        return;
+    }
     if (kind == RNG_MWC32) {
         uint32_t x, c;
         draw_mwc(z, a[s], x, c);
