@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (batched, serving, other configs)")
     p.add_argument("--workload", default="full",
-                   choices=["full", "batched", "serving", "inline"])
+                   choices=["full", "batched", "serving", "inline", "paper"])
     p.add_argument("--rate", type=float, default=20_000.0, help="serving: arrivals/s")
     p.add_argument("--duration", type=float, default=10.0, help="serving: seconds")
     p.add_argument("--verify-every", type=int, default=100, help="serving: check every k-th")
@@ -784,6 +784,32 @@ def run_inline(clock_mhz: float):
     return res
 
 
+# The paper's rates on a GTX280 (GSamples/s, uint32; Tables I-III), for
+# context only: another card, another year.
+PAPER_GTX280 = {"mwc16x2": {"with_writeback": 18.0, "without_writeback": 37.5},
+                "xorshift8": {"with_writeback": 12.5, "without_writeback": 14.5},
+                "kiss_xor": {"with_writeback": 9.2, "without_writeback": 19.1}}
+
+
+def run_paper_variants():
+    """The paper's own generators: writeback (uint32 to HBM) and inline (sum
+    consumer) rates.  The two MWC-pair kinds have at most 76,636 streams (the
+    pairs of 392 multipliers), so they run 76,636 x 16,384 per call, cut into
+    jumped segments; XORSHIFT8 runs 2^22 x 1024 like the target kinds."""
+    from paper_1101_1846_gb300 import capi
+    res = {}
+    for kind, name, n, steps in ((3, "mwc16x2", capi.RNG_MAX_STREAMS_MWC16, 16384),
+                                 (4, "xorshift8", 1 << 22, 1024),
+                                 (5, "kiss_xor", capi.RNG_MAX_STREAMS_MWC16, 16384)):
+        w = _plain_rate(kind, n, steps, 0, 21)
+        r = _reduce_rate(kind, n, steps, capi.RNG_SUM_U32, 21)
+        res[name] = {"workload": f"{n} streams x {steps} outputs",
+                     "with_writeback": {**w, "tb_s": 4 * n * steps / (w["ms"] * 1e-3) / 1e12},
+                     "without_writeback_sum": r,
+                     "paper_gtx280_gsamples_s": PAPER_GTX280[name]}
+    return res
+
+
 def run_extras(args, clock_mhz: float = 2070.0):
     """The other workloads, summarised for the same JSON line: the 2^20 x 1024
     xor128/KISS calls, the 4096 x 4096 MWC call (few streams: split into
@@ -796,6 +822,7 @@ def run_extras(args, clock_mhz: float = 2070.0):
                                                                           fmt, 7)
     extras["other_configs"]["mwc_u32_4096x4096"] = _plain_rate(0, 4096, 4096, 0, 42)
     extras["inline"] = run_inline(clock_mhz)
+    extras["paper_variants"] = run_paper_variants()
     keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
             "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
             "batched_ms", "gpu_launches")
@@ -820,6 +847,8 @@ def main():
         print(json.dumps(run_serving(args)))
     elif args.workload == "inline":
         print(json.dumps(run_inline(2070.0)))
+    elif args.workload == "paper":
+        print(json.dumps(run_paper_variants()))
     else:
         run_ours(args)
 

@@ -104,16 +104,25 @@ gen_shift(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
 // arrival that brings the count to segments + 1 sees every read done and the
 // final state ready: it writes the state (from registers or the stash) and
 // clears the counter for the next call.
-template <int KIND, int FMT, int HINT>
+//
+// SYNC: rows 16- but not 32-byte aligned.  As in body_vec_sync, a barrier
+// every four rows keeps the CTA's warps together so that the two halves of
+// a shared DRAM sector meet in L2; every thread of the CTA then runs the
+// rows (a CTA shares its segment, hence its jump and its row count), and
+// threads past the last group store nothing and count no arrival.
+template <int KIND, int FMT, int HINT, bool SYNC>
 __global__ void __launch_bounds__(256)
 gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
           uint32_t steps, uint32_t rows, uint32_t *__restrict__ out, uint64_t ld,
           uint64_t s_begin, uint64_t count, uint32_t *__restrict__ stash,
           uint32_t *__restrict__ counters, const uint64_t *__restrict__ jmul, JumpTables T)
 {
-    const uint64_t c_first = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (c_first >= count)
+    uint64_t c_first = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const bool live = c_first < count;
+    if (!SYNC && !live)
         return;
+    if (!live)
+        c_first = 0;  // compute on stream 0's state, never store
     constexpr int W = KindTraits<KIND>::W;
     const uint64_t s0 = s_begin + c_first;
     const uint32_t segs = gridDim.y;
@@ -129,7 +138,7 @@ gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
         load4(mult + s0, a);
     __threadfence();  // the reads above are done before the arrival is counted
     uint32_t *cnt = counters + s0 / 4;
-    bool finish = atomicAdd(cnt, 1u) == segs;
+    const bool finish = live && atomicAdd(cnt, 1u) == segs;
     if (finish) {
         // every other arrival, the stash included, came first
         __threadfence();
@@ -154,14 +163,30 @@ gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
         jump_streams<KIND, 4, KIND == RNG_MWC32 || KIND == RNG_KISS>(w, a, first, T);
     }
     uint32_t *row = out + (uint64_t)first * ld + c_first;
+    if constexpr (SYNC) {
+        for (uint32_t j = 0; j < mine; ++j) {
+            if ((j & 3) == 0)
+                __syncthreads();
+            const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+            const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+            const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+            const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+            if (live)
+                store16<HINT>(row, o0, o1, o2, o3);
+            row += ld;
+        }
+        if (!live)
+            return;  // after the last barrier
+    } else {
 #pragma unroll 4
-    for (uint32_t j = 0; j < mine; ++j) {
-        const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
-        const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
-        const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
-        const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
-        store16<HINT>(row, o0, o1, o2, o3);
-        row += ld;
+        for (uint32_t j = 0; j < mine; ++j) {
+            const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+            const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+            const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+            const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+            store16<HINT>(row, o0, o1, o2, o3);
+            row += ld;
+        }
     }
     if (y == segs - 1) {
 #pragma unroll
@@ -241,7 +266,7 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
     uint32_t *out = static_cast<uint32_t *>(p.out);
     uint64_t L = 0, S = 0;
     Gen *g = p.owner;
-    if (g && g->d_split && sectors &&
+    if (g && g->d_split && aligned &&
         split_plan(KIND, count, p.steps, 4, g->jmul_segs, &L, &S)) {
         JumpTables T{};
         const uint64_t *jmul = nullptr;
@@ -250,9 +275,20 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
             e = mwc_jump_table(g, L, st, &jmul);
         if (e)
             return e;
-        auto fn = fmt == RNG_F32
-                      ? (sh.hint ? gen_split<KIND, RNG_F32, 1> : gen_split<KIND, RNG_F32, 0>)
-                      : (sh.hint ? gen_split<KIND, RNG_U32, 1> : gen_split<KIND, RNG_U32, 0>);
+        using SplitFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t,
+                                 uint32_t *, uint64_t, uint64_t, uint64_t, uint32_t *,
+                                 uint32_t *, const uint64_t *, JumpTables);
+        SplitFn fn;
+        if (sectors)
+            fn = fmt == RNG_F32 ? (sh.hint ? gen_split<KIND, RNG_F32, 1, false>
+                                           : gen_split<KIND, RNG_F32, 0, false>)
+                                : (sh.hint ? gen_split<KIND, RNG_U32, 1, false>
+                                           : gen_split<KIND, RNG_U32, 0, false>);
+        else
+            fn = fmt == RNG_F32 ? (sh.hint ? gen_split<KIND, RNG_F32, 1, true>
+                                           : gen_split<KIND, RNG_F32, 0, true>)
+                                : (sh.hint ? gen_split<KIND, RNG_U32, 1, true>
+                                           : gen_split<KIND, RNG_U32, 0, true>);
         const dim3 grid((unsigned)((count / 4 + 255) / 256), (unsigned)S);
         fn<<<grid, 256, 0, st>>>(p.state, p.a, p.n, (uint32_t)p.steps, (uint32_t)L, out, p.ld,
                                  p.s_begin, count, g->d_split, g->d_cnt, jmul, T);

@@ -167,7 +167,10 @@ def test_jump_then_generate_equals_stepping(kind):
 # ------------------------------------------------------ split generation
 @pytest.mark.parametrize("kind,n,steps", [(oracle.MWC, 64, 5000), (oracle.KISS, 64, 5000),
                                           (oracle.XOR128, 8, 20000), (oracle.KISS, 8, 300),
-                                          (oracle.MWC, 4, 100_000)])
+                                          (oracle.MWC, 4, 100_000),
+                                          # rows 16- but not 32-byte aligned: barrier-synced
+                                          (oracle.MWC, 12, 5000), (oracle.KISS, 20, 3000),
+                                          (oracle.XOR128, 12, 5000)])
 @pytest.mark.parametrize("fmt", [oracle.U32, oracle.F32])
 def test_split_generate_equals_oracle(kind, n, steps, fmt):
     seed = 17

@@ -101,7 +101,10 @@ def test_unaligned_rows_and_ranges(kind):
 
 @pytest.mark.parametrize("kind,n,steps", [(oracle.MWC16X2, 8, 5000), (oracle.KISS_XOR, 64, 4096),
                                           (oracle.XORSHIFT8, 8, 3000),
-                                          (oracle.MWC16X2, 4096, 1000)])
+                                          (oracle.MWC16X2, 4096, 1000),
+                                          # every pair; rows 16- but not 32-byte aligned
+                                          (oracle.MWC16X2, 76636, 600),
+                                          (oracle.KISS_XOR, 76636, 600)])
 def test_few_streams_long_sequences(kind, n, steps):
     # MWC16X2 and KISS_XOR split into jumped segments; XORSHIFT8 does not
     seed = 9
