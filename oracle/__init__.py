@@ -129,6 +129,10 @@ def _load(path: Path):
         "oracle_xorshift32_jump": (None, [_u32p, u64]),
         "oracle_lcg_jump": (None, [_u32p, u64]),
         "oracle_jump": (None, [i32, u32, _u32p, u64]),
+        "oracle_bat_ones": (u64, [_u32p, u64]),
+        "oracle_bat_bytes": (None, [_u32p, u64, _u64p]),
+        "oracle_bat_serial": (None, [_u32p, u64, u64, _u64p]),
+        "oracle_bat_birthday": (u64, [_u32p, u64, u64, _u64p]),
         "oracle_mwc_period": (u64, [u32, u32, u32, i32, u64]),
         "oracle_xorshift32_period": (u64, [u32]),
         "oracle_lcg_period": (u64, [u32]),
@@ -404,6 +408,23 @@ def lcg_jump(z: int, k: int) -> int:
     Z = ctypes.c_uint32(z)
     lib().oracle_lcg_jump(ctypes.byref(Z), k)
     return int(Z.value)
+
+
+# --------------------------------------------------------------- battery
+def battery_counts(u: np.ndarray) -> dict:
+    """Counts of the four battery tests over u of shape (n_per_stream,
+    n_streams), stream-interleaved uint32."""
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    rows, n = u.shape
+    byte, serial, bday = (np.zeros(256, np.uint64), np.zeros(256, np.uint64),
+                          np.zeros(16, np.uint64))
+    L = lib()
+    ones = int(L.oracle_bat_ones(_p32(u), u.size))
+    L.oracle_bat_bytes(_p32(u), u.size, _p64(byte))
+    L.oracle_bat_serial(_p32(u), n, rows, _p64(serial))
+    samples = int(L.oracle_bat_birthday(_p32(u), n, rows, _p64(bday)))
+    return {"n_outputs": int(u.size), "ones": ones, "bytes": byte, "serial": serial,
+            "birthday_samples": samples, "birthday": bday}
 
 
 # ---------------------------------------------------------------- periods

@@ -38,6 +38,9 @@
  *                                    (I+L^24)(I+R^7) is parity unpinned: both
  *                                    orders have full period
  *     KISS, xor form ............... pinned (parts stepped on their own)
+ *   battery counts ................. pinned (closed-form counts of synthetic
+ *                                    outputs; birthday samples built from
+ *                                    spacing lists with known repeats)
  */
 #include "oracle.h"
 
@@ -808,4 +811,88 @@ void oracle_jump(int kind, uint32_t a, uint32_t *st, uint64_t k)
         oracle_xorshift32_jump(&st[2], k);
         oracle_lcg_jump(&st[3], k);
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* A small statistical battery: counts over a block of outputs u laid out
+ * stream-interleaved (u[j * n_streams + s], j < n_per_stream).  The paper
+ * assesses its generators with DIEHARD and TestU01 (Sec. "Performance
+ * evaluation"); these are four tests of those families, written from their
+ * definitions; the statistics and p-values are formed from the counts.  */
+/* ------------------------------------------------------------------ */
+
+/* Monobit: the number of one bits in all outputs. */
+uint64_t oracle_bat_ones(const uint32_t *u, uint64_t count)
+{
+    uint64_t ones = 0;
+    for (uint64_t i = 0; i < count; ++i) {
+        uint32_t v = u[i];
+        while (v) {
+            ones += v & 1u;
+            v >>= 1;
+        }
+    }
+    return ones;
+}
+
+/* Frequency: histogram of the top 8 bits of every output (256 bins). */
+void oracle_bat_bytes(const uint32_t *u, uint64_t count, uint64_t hist[256])
+{
+    memset(hist, 0, 256 * sizeof(uint64_t));
+    for (uint64_t i = 0; i < count; ++i)
+        hist[u[i] >> 24]++;
+}
+
+/* Serial: each stream's outputs taken in non-overlapping consecutive pairs
+ * (u_{2k}, u_{2k+1}); the cell is the top 4 bits of the first and of the
+ * second, 16 x 16 cells. */
+void oracle_bat_serial(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
+                       uint64_t hist[256])
+{
+    memset(hist, 0, 256 * sizeof(uint64_t));
+    for (uint64_t s = 0; s < n_streams; ++s)
+        for (uint64_t j = 0; j + 1 < n_per_stream; j += 2) {
+            uint32_t a = u[j * n_streams + s] >> 28;
+            uint32_t b = u[(j + 1) * n_streams + s] >> 28;
+            hist[a * 16 + b]++;
+        }
+}
+
+static int cmp_u32(const void *x, const void *y)
+{
+    uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
+    return a < b ? -1 : a > b;
+}
+
+/* Birthday spacings (Marsaglia): m = 512 birthdays in a year of 2^24 days,
+ * the top 24 bits of 512 consecutive outputs of one stream.  Sort them; the
+ * spacings are the first birthday and the differences of neighbours (m
+ * values); sort the spacings; the statistic is the number of spacings equal
+ * to the one before them.  It is asymptotically Poisson with mean
+ * m^3 / (4 * 2^24) = 2.  Samples are the blocks of 512 outputs of each
+ * stream (floor(n_per_stream / 512) per stream); hist[k] counts samples
+ * with k repeats, k < 15, and hist[15] those with 15 or more.  Returns the
+ * number of samples. */
+uint64_t oracle_bat_birthday(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
+                             uint64_t hist[16])
+{
+    uint32_t b[512], d[512];
+    uint64_t samples = 0;
+    memset(hist, 0, 16 * sizeof(uint64_t));
+    for (uint64_t s = 0; s < n_streams; ++s)
+        for (uint64_t blk = 0; (blk + 1) * 512 <= n_per_stream; ++blk) {
+            for (int i = 0; i < 512; ++i)
+                b[i] = u[(blk * 512 + i) * n_streams + s] >> 8;
+            qsort(b, 512, sizeof(uint32_t), cmp_u32);
+            d[0] = b[0];
+            for (int i = 1; i < 512; ++i)
+                d[i] = b[i] - b[i - 1];
+            qsort(d, 512, sizeof(uint32_t), cmp_u32);
+            int repeats = 0;
+            for (int i = 1; i < 512; ++i)
+                repeats += d[i] == d[i - 1];
+            hist[repeats < 15 ? repeats : 15]++;
+            ++samples;
+        }
+    return samples;
 }

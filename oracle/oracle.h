@@ -95,6 +95,15 @@ void oracle_xorshift8_jump(uint32_t st[8], uint64_t k);
 void oracle_lcg_jump(uint32_t *z, uint64_t k);
 void oracle_jump(int kind, uint32_t a, uint32_t *st, uint64_t k);
 
+/* statistical battery counts over stream-interleaved outputs (the paper's
+ * randomness assessment, Sec. "Performance evaluation") */
+uint64_t oracle_bat_ones(const uint32_t *u, uint64_t count);
+void oracle_bat_bytes(const uint32_t *u, uint64_t count, uint64_t hist[256]);
+void oracle_bat_serial(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
+                       uint64_t hist[256]);
+uint64_t oracle_bat_birthday(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
+                             uint64_t hist[16]);
+
 /* brute-force periods (pins) */
 uint64_t oracle_mwc_period(uint32_t a, uint32_t x0, uint32_t c0, int log2b,
                            uint64_t limit);

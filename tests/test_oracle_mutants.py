@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_battery as bat
 import test_oracle_consumers_jump as cj
 import test_oracle_paper_variants as pv
 import test_oracle_pins as pins
@@ -85,6 +86,14 @@ MUTANTS = [
      pv.check_kiss_xor_is_parts),
     ("multiplier pairs reversed", "out[found++] = table[i] | (table[j] << 16);",
      "out[found++] = table[j] | (table[i] << 16);", pv.check_mwc16_pairs_lexicographic),
+    ("frequency bins on 7 bits", "hist[u[i] >> 24]++;", "hist[u[i] >> 25]++;",
+     bat.check_ones_and_bytes),
+    ("serial pairs overlap", "for (uint64_t j = 0; j + 1 < n_per_stream; j += 2) {",
+     "for (uint64_t j = 0; j + 1 < n_per_stream; j += 1) {", bat.check_serial_pairs_within_streams),
+    ("birthday repeats of days, not spacings", "repeats += d[i] == d[i - 1];",
+     "repeats += b[i] == b[i - 1];", bat.check_birthday_repeats),
+    ("birthday days of 25 bits", "b[i] = u[(blk * 512 + i) * n_streams + s] >> 8;",
+     "b[i] = u[(blk * 512 + i) * n_streams + s] >> 7;", bat.check_birthday_repeats),
 ]
 
 
