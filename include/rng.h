@@ -236,6 +236,36 @@ int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, void *out);
  * it (Sec. "Parallelizing RNGs"). */
 int rng_jump(rng_handle h, uint64_t k);
 
+/* Counts of a small statistical battery (rng_battery). */
+typedef struct rng_battery_counts {
+    uint64_t n_outputs;        /* outputs counted                              */
+    uint64_t ones;             /* monobit: one bits in all outputs             */
+    uint64_t bytes[256];       /* frequency: outputs by their top 8 bits       */
+    uint64_t serial[256];      /* serial: non-overlapping pairs (u_2k, u_2k+1)
+                                  of a stream by (u_2k >> 28) * 16 + (u_2k+1 >> 28) */
+    uint64_t birthday_samples; /* birthday spacings: samples (512 consecutive
+                                  outputs of a stream; floor(n_per_stream/512)
+                                  per stream)                                 */
+    uint64_t birthday[16];     /* samples by repeated spacings (15: 15 or more):
+                                  days = top 24 bits, sorted; spacings = the
+                                  first day and neighbour differences, sorted;
+                                  repeats = spacings equal to the one before.
+                                  Asymptotically Poisson with mean
+                                  512^3 / (4 * 2^24) = 2                      */
+} rng_battery_counts;
+
+/* Counts the battery over generator outputs in device memory: `dev_u`
+ * (DEVICE, uint32, 4-byte aligned) holds n_per_stream rows of n_streams
+ * outputs, output j of stream s at dev_u[j * n_streams + s] (rng_generate's
+ * layout); the counts go to *host_counts (HOST).  Runs on cuda_stream and
+ * SYNCHRONISES it; allocates a few KB of device memory for the call.
+ * Errors: RNG_ERR_ARG, RNG_ERR_OOM, RNG_ERR_CUDA.
+ * Paper: the generators' randomness is assessed with DIEHARD and TestU01
+ * (Sec. "Performance evaluation"); these four tests come from those
+ * families (monobit, frequency, serial, Marsaglia's birthday spacings). */
+int rng_battery(const void *dev_u, uint64_t n_streams, uint64_t n_per_stream,
+                rng_battery_counts *host_counts, void *cuda_stream);
+
 /* Where a handle's state lives, for kernels that step the streams
  * themselves (include/gbrng_device.cuh, Engine<KIND>). */
 typedef struct rng_device_view {

@@ -23,7 +23,7 @@ LIBDIR = PKG / "_lib"
 LIB = LIBDIR / "libgbrng.so"
 
 SOURCES = ["api.cu", "multipliers.cu", "seed.cu", "generate.cu", "generate_paper.cu", "batch.cu",
-           "probe.cu", "serve.cu", "jump.cu", "reduce.cu"]
+           "probe.cu", "serve.cu", "jump.cu", "reduce.cu", "battery.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-Xcompiler", "-Wall", "-I", str(INCLUDE), "-I", str(CSRC)]

@@ -41,6 +41,12 @@ class rng_device_view(ctypes.Structure):
                 ("state", ctypes.c_void_p), ("mult", ctypes.c_void_p)]
 
 
+class rng_battery_counts(ctypes.Structure):
+    _fields_ = [("n_outputs", ctypes.c_uint64), ("ones", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64 * 256), ("serial", ctypes.c_uint64 * 256),
+                ("birthday_samples", ctypes.c_uint64), ("birthday", ctypes.c_uint64 * 16)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/*.h
 SIGNATURES = {
     "rng_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]),
@@ -62,6 +68,8 @@ SIGNATURES = {
     "rng_generate_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                            ctypes.c_void_p]),
     "rng_jump": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rng_battery": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.POINTER(rng_battery_counts), ctypes.c_void_p]),
     "rng_get_device_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(rng_device_view)]),
     "rng_plan_create": (ctypes.c_void_p, [ctypes.POINTER(rng_batch_item), ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int]),
