@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (batched, serving, other configs)")
     p.add_argument("--workload", default="full",
-                   choices=["full", "batched", "serving", "inline", "paper"])
+                   choices=["full", "batched", "serving", "inline", "paper", "battery"])
     p.add_argument("--rate", type=float, default=20_000.0, help="serving: arrivals/s")
     p.add_argument("--duration", type=float, default=10.0, help="serving: seconds")
     p.add_argument("--verify-every", type=int, default=100, help="serving: check every k-th")
@@ -84,10 +84,16 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("include/gbrng_device.cuh", "paper_1101_1846_gb300/csrc/gen_body.cuh",
+                  "paper_1101_1846_gb300/csrc/gen_kernels.cuh",
+                  "paper_1101_1846_gb300/csrc/generate.cu", "paper_1101_1846_gb300/csrc/gbrng.cuh")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the files the generate kernels are compiled from."""
     h = hashlib.sha256()
-    for name in ("gen_body.cuh", "generate.cu", "gbrng.cuh"):
-        h.update((ROOT / "paper_1101_1846_gb300" / "csrc" / name).read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -810,6 +816,34 @@ def run_paper_variants():
     return res
 
 
+def run_battery():
+    """The battery's p-values for every kind over 2^20 streams x 1024
+    uint32 outputs (the pair kinds: 76,636 x 16,384), and the time of the
+    counting call."""
+    import torch
+
+    from paper_1101_1846_gb300 import battery, capi
+    from paper_1101_1846_gb300.generator import Generator
+    names = {0: "mwc", 1: "xor128", 2: "kiss", 3: "mwc16x2", 4: "xorshift8", 5: "kiss_xor"}
+    res = {}
+    for kind, name in names.items():
+        n, rows = ((capi.RNG_MAX_STREAMS_MWC16, 16384) if kind in (3, 5) else (1 << 20, 1024))
+        g = Generator(kind, n, 99)
+        u = g.generate(rows)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = battery.counts(u, n, rows)
+        dt = time.perf_counter() - t0
+        st = battery.statistics(c)
+        res[name] = {"outputs": n * rows, "count_ms": dt * 1e3, "passed": battery.passed(st),
+                     **{k: round(v["p"], 6) for k, v in st.items()},
+                     "birthday_samples": st["birthday"]["samples"]}
+        del u
+        g.close()
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_extras(args, clock_mhz: float = 2070.0):
     """The other workloads, summarised for the same JSON line: the 2^20 x 1024
     xor128/KISS calls, the 4096 x 4096 MWC call (few streams: split into
@@ -823,6 +857,7 @@ def run_extras(args, clock_mhz: float = 2070.0):
     extras["other_configs"]["mwc_u32_4096x4096"] = _plain_rate(0, 4096, 4096, 0, 42)
     extras["inline"] = run_inline(clock_mhz)
     extras["paper_variants"] = run_paper_variants()
+    extras["battery"] = run_battery()
     keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
             "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
             "batched_ms", "gpu_launches")
@@ -849,6 +884,8 @@ def main():
         print(json.dumps(run_inline(2070.0)))
     elif args.workload == "paper":
         print(json.dumps(run_paper_variants()))
+    elif args.workload == "battery":
+        print(json.dumps(run_battery()))
     else:
         run_ours(args)
 
