@@ -236,6 +236,12 @@ int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, void *out);
  * it (Sec. "Parallelizing RNGs"). */
 int rng_jump(rng_handle h, uint64_t k);
 
+/* Most birthday-spacings samples rng_battery takes: at 512 days in a year
+ * of 2^24 the repeat count's mean is about 0.3 % below the Poisson limit of
+ * 2 it is compared with, a bias that millions of samples would detect but
+ * a few thousand cannot (DIEHARD takes a few hundred). */
+#define RNG_BATTERY_BIRTHDAY_MAX 4096
+
 /* Counts of a small statistical battery (rng_battery). */
 typedef struct rng_battery_counts {
     uint64_t n_outputs;        /* outputs counted                              */
@@ -243,9 +249,11 @@ typedef struct rng_battery_counts {
     uint64_t bytes[256];       /* frequency: outputs by their top 8 bits       */
     uint64_t serial[256];      /* serial: non-overlapping pairs (u_2k, u_2k+1)
                                   of a stream by (u_2k >> 28) * 16 + (u_2k+1 >> 28) */
-    uint64_t birthday_samples; /* birthday spacings: samples (512 consecutive
-                                  outputs of a stream; floor(n_per_stream/512)
-                                  per stream)                                 */
+    uint64_t birthday_samples; /* birthday spacings: samples of 512
+                                  consecutive outputs of a stream; sample i is
+                                  block i / n_streams of stream i % n_streams,
+                                  for i < min(floor(n_per_stream / 512) *
+                                  n_streams, RNG_BATTERY_BIRTHDAY_MAX)       */
     uint64_t birthday[16];     /* samples by repeated spacings (15: 15 or more):
                                   days = top 24 bits, sorted; spacings = the
                                   first day and neighbour differences, sorted;

@@ -101,6 +101,7 @@ uint64_t oracle_bat_ones(const uint32_t *u, uint64_t count);
 void oracle_bat_bytes(const uint32_t *u, uint64_t count, uint64_t hist[256]);
 void oracle_bat_serial(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
                        uint64_t hist[256]);
+#define ORACLE_BAT_BIRTHDAY_MAX 4096
 uint64_t oracle_bat_birthday(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
                              uint64_t hist[16]);
 

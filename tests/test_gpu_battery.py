@@ -38,12 +38,14 @@ def same(a: dict, b: dict):
 
 
 @pytest.mark.parametrize("kind", ALL)
-@pytest.mark.parametrize("n,rows", [(300, 1537), (1024, 1024), (7, 2049)])
+@pytest.mark.parametrize("n,rows", [(300, 1537), (1024, 1024), (7, 2049), (3000, 1024)])
 def test_counts_equal_oracle_on_oracle_outputs(kind, n, rows):
     a = oracle.multipliers_for(kind, n)
     st = oracle.seed_streams(kind, a, 77 + n, np.arange(n))
     u, _ = oracle.generate(kind, a, st, rows, oracle.U32)
-    same(device_counts(u), oracle.battery_counts(u))
+    c = device_counts(u)
+    same(c, oracle.battery_counts(u))
+    assert c["birthday_samples"] == min((rows // 512) * n, capi.RNG_BATTERY_BIRTHDAY_MAX)
 
 
 def test_counts_of_designed_samples():

@@ -70,8 +70,7 @@ def check_birthday_repeats():
             sp[i] = sp[-1 - (i % 5)]  # copies of five values never replaced
         assert 512 - len(np.unique(sp)) == r
         streams.append(sp)
-    # two streams of three 512-output blocks and two of three blocks... lay
-    # the 12 samples out as 4 streams x 3 blocks
+    # the 12 samples laid out as 4 streams x 3 blocks
     cols = []
     for s in range(4):
         cols.append(np.concatenate([_birthday_sample(streams[3 * s + b], rng) for b in range(3)]))
@@ -83,6 +82,34 @@ def check_birthday_repeats():
         for b in range(3):
             expect[min(want[3 * s + b], 15)] += 1
     assert c["birthday_samples"] == 12
+    assert np.array_equal(c["birthday"], expect)
+
+
+def check_birthday_cap_and_order():
+    """At most 4096 samples, taken block by block across the streams: with
+    3000 streams of two blocks, the samples are block 0 of every stream and
+    block 1 of streams 0..1095.  Each sample's repeat count encodes where it
+    came from."""
+    rng = np.random.Generator(np.random.PCG64(23))
+    n = 3000
+    base = rng.permutation(np.arange(1, 513, dtype=np.int64))
+
+    def sample(r):
+        sp = base.copy()
+        for i in range(r):
+            sp[i] = sp[-1 - (i % 5)]
+        b = np.cumsum(sp.astype(np.uint64))
+        return ((b << np.uint64(8)) | np.uint64(3)).astype(np.uint32)
+
+    r_of = {(0, "lo"): 1, (1, "lo"): 2, (1, "hi"): 9}
+    blk0 = sample(1)
+    b1_lo, b1_hi = sample(2), sample(9)
+    cols = [np.concatenate([blk0, b1_lo if s < 1096 else b1_hi]) for s in range(n)]
+    c = oracle.battery_counts(_interleave(cols))
+    assert c["birthday_samples"] == 4096
+    expect = np.zeros(16, np.uint64)
+    expect[r_of[(0, "lo")]] = n
+    expect[r_of[(1, "lo")]] = 4096 - n
     assert np.array_equal(c["birthday"], expect)
 
 
@@ -128,6 +155,10 @@ def test_serial_pairs_within_streams():
 
 def test_birthday_repeats():
     check_birthday_repeats()
+
+
+def test_birthday_cap_and_order():
+    check_birthday_cap_and_order()
 
 
 def test_statistics_on_kiss_and_a_weyl_sequence():

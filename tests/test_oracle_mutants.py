@@ -94,6 +94,8 @@ MUTANTS = [
      "repeats += b[i] == b[i - 1];", bat.check_birthday_repeats),
     ("birthday days of 25 bits", "b[i] = u[(blk * 512 + i) * n_streams + s] >> 8;",
      "b[i] = u[(blk * 512 + i) * n_streams + s] >> 7;", bat.check_birthday_repeats),
+    ("birthday without the sample cap", "s < n_streams && samples < ORACLE_BAT_BIRTHDAY_MAX;",
+     "s < n_streams;", bat.check_birthday_cap_and_order),
 ]
 
 
