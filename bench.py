@@ -861,8 +861,7 @@ def run_extras(args, clock_mhz: float = 2070.0):
     keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
             "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
             "batched_ms", "gpu_launches")
-    args.tune = True  # pick the plan shape for this GPU (a few timed launches)
-    b = run_batched(args)
+    b = run_batched(args)  # the library's default plan shape (--tune to sweep shapes)
     extras["batched"] = {k: b[k] for k in keep if k in b}
     extras["batched"]["over_plain_full_device"] = None
     s = run_serving(args)

@@ -328,7 +328,7 @@ typedef struct rng_plan *rng_plan_handle;
  * of 4 * threads streams when its rows are 16-byte aligned, else of
  * 4 * (31 * threads / 32 + 1) streams (the last (s_end - s_begin) % 4
  * streams of such an item form a tile of their own), the tiles are ordered by length, largest first, and
- * the work list is copied to the device (synchronises).  threads = CTA size (power of two, 32..512; 0 = 128),
+ * the work list is copied to the device (synchronises).  threads = CTA size (power of two, 32..512; 0 = 512),
  * ctas_per_sm = resident CTAs the persistent grid puts on each SM (1..32;
  * 0 = as many as fit).  Items of the same handle must cover disjoint stream
  * ranges (they then run side by side); items with n_per_stream = 0 are
