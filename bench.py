@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--lanes", type=int, default=2,
                    help="batched: groups of instances whose waves overlap")
     p.add_argument("--no-verify", action="store_true", help="batched: skip the check pass")
-    p.add_argument("--chunk-rows", type=int, default=512,
+    p.add_argument("--chunk-rows", type=int, default=256,
                    help="batched: rows per piece (0 = whole instances)")
     return p.parse_args()
 
@@ -251,7 +251,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1101_1846_gb300 import capi
+    from paper_1101_1846_gb300 import capi, replicas
     from paper_1101_1846_gb300.generator import Generator
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,7 +269,7 @@ def run_ours(args):
             dist.barrier()
 
     # weak scaling: every rank owns its own n streams, seeds shifted by rank*n
-    gens = {k: Generator(k, n, args.seed + rank * n) for k in KINDS}
+    gens = {k: Generator(k, n, replicas.rank_seed(args.seed, rank, n)) for k in KINDS}
     out = torch.empty((steps, n), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     pairs = [(k, f) for k in KINDS for f in FMTS]
@@ -304,12 +304,9 @@ def run_ours(args):
     barrier()
     clock_info = clocks.stop()
     ms = t_start.elapsed_time(t_end)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = replicas.max_over_ranks(ms, device="cuda")
     samples = world * args.steps * len(pairs) * n * steps
-    value = samples / (ms_max * 1e-3) / 1e9
+    value = replicas.job_rate(args.steps * len(pairs) * n * steps, world, ms_max * 1e-3) / 1e9
 
     per_kernel = {}
     for (k, f), (s_ev, e_ev) in events.items():
@@ -358,10 +355,7 @@ def run_ours(args):
                 gens[k].generate_host(steps, f, out=host)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        dt_t = torch.tensor([dt], device="cuda")
-        if world > 1:
-            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
-        dt = float(dt_t.item())
+        dt = replicas.max_over_ranks(dt, device="cuda")
         e2e_samples = world * args.e2e_steps * len(pairs) * n * steps
         e2e = {"value": e2e_samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": len(pairs) * n * steps * 4,
