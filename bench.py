@@ -749,6 +749,38 @@ def _jump_ms(kind, n, k, seed, reps=5):
     return sorted(ts)[len(ts) // 2]
 
 
+def run_int_probes(clock_mhz: float):
+    """Integer-pipe probes (gbrng_probe_int): 8 independent chains per
+    thread of one operation, 1216 CTAs x 256 threads.  Returns, per op, the
+    operations per second and the lane-instructions per SM per clock."""
+    import ctypes
+
+    import torch
+
+    from paper_1101_1846_gb300 import capi
+    blocks, threads, iters = SMS * 8, 256, 1 << 13
+    sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    names = {0: ("mwc_step", 2), 1: ("lcg_mad", 1), 2: ("shift_xor", 2), 3: ("add", 1)}
+    res = {}
+    for op, (name, instr) in names.items():
+        def launch():
+            capi.check(capi.lib().gbrng_probe_int(op, ctypes.c_void_p(sink.data_ptr()), blocks,
+                                                  threads, iters, ctypes.c_void_p(s.cuda_stream)))
+        launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        launch()
+        b.record(s)
+        b.synchronize()
+        sec = a.elapsed_time(b) * 1e-3
+        ops = blocks * threads * iters * 8 / sec
+        res[name] = {"ops_per_s": ops, "instr_per_op": instr,
+                     "lane_instr_per_sm_clk": ops * instr / (SMS * clock_mhz * 1e6)}
+    return res
+
+
 def run_inline(clock_mhz: float):
     """The generators with the numbers used in registers (no output array):
     per kind, the sum consumer and the quarter-disc count at 2^22 streams x
@@ -772,6 +804,10 @@ def run_inline(clock_mhz: float):
             "roofline": {"bound": "alu", "achieved": tops, "peak": peak, "unit": "Tops/s",
                          "frac": tops / peak, "ops_per_sample": ops},
             "jump_2^22_streams_by_2^40+1_ms": _jump_ms(kind, n, (1 << 40) + 1, 5)}
+    probes = run_int_probes(clock_mhz)
+    res["int_probes"] = probes
+    mwc = res["kinds"]["mwc"]["sum_u32"]["gsamples_s"] * 1e9
+    res["kinds"]["mwc"]["of_probed_mwc_step_rate"] = mwc / probes["mwc_step"]["ops_per_s"]
     # few streams: the 4096 x 4096 MWC call with and without splitting
     v = ctypes.c_int()
     capi.check(capi.lib().gbrng_get_split(0, ctypes.byref(v)))

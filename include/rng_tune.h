@@ -37,12 +37,14 @@ int gbrng_get_split(int kind, int *log2_rows);
 int gbrng_probe_write(void *dst, uint64_t bytes, int blocks, int threads, int hint,
                       int reps, void *cuda_stream);
 
-/* Integer-pipe probe: every thread runs `iters` dependent-free iterations of
- * `op` on 8 independent chains (op 0 = 32x32->64 multiply-add as in one MWC
- * step, op 1 = 32-bit multiply-add as in the LCG, op 2 = shift+xor as in a
- * xorshift step, op 3 = 32-bit add) and writes one word per thread to `sink`
- * (DEVICE, blocks*threads uint32).  Asynchronous.  Used to measure the
- * integer throughput the generators can reach (the paper's U_ops, Eq. 9). */
+/* Integer-pipe probe: every thread runs `iters` iterations of `op` on each
+ * of 8 independent chains (op 0 = 32x32->64 multiply-add as in one MWC step,
+ * 2 instructions; op 1 = 32-bit multiply-add as in the LCG, 1; op 2 =
+ * shift + xor as in a xorshift step, 2; op 3 = 32-bit add, 1), each written
+ * as volatile inline PTX so that none is folded or dropped, and writes one
+ * word per thread to `sink` (DEVICE, blocks*threads uint32).  Asynchronous.
+ * Used to measure the integer throughput the generators can reach (the
+ * paper's U_ops, Eq. 9). */
 int gbrng_probe_int(int op, uint32_t *sink, int blocks, int threads, uint64_t iters,
                     void *cuda_stream);
 

@@ -25,7 +25,16 @@ __global__ void probe_write(uint4 *dst, uint64_t n16, int reps)
     }
 }
 
-// 8 independent chains per thread so that latency is hidden by ILP.
+// Integer-pipe probes: every thread runs 8 independent chains (latency
+// hidden by ILP) of one operation.  Each operation is inline PTX marked
+// volatile, so the compiler neither folds repeated applications (affine and
+// GF(2) maps compose into one) nor drops them; the chains feed one word per
+// thread written to `sink` so that nothing is dead.
+//   op 0  32 x 32 + 32 -> 64 multiply-add as in an MWC step (mad.lo.cc +
+//         madc.hi: 2 instructions)
+//   op 1  32-bit multiply-add as in the LCG (mad.lo: 1 instruction)
+//   op 2  shift and xor as in a xorshift step (shl + xor: 2 instructions)
+//   op 3  32-bit add (1 instruction)
 template <int OP>
 __global__ void probe_int(uint32_t *sink, uint64_t iters)
 {
@@ -40,15 +49,20 @@ __global__ void probe_int(uint32_t *sink, uint64_t iters)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             if constexpr (OP == 0) {
-                uint64_t t = (uint64_t)a * x[k] + c[k];
-                x[k] = (uint32_t)t;
-                c[k] = (uint32_t)(t >> 32);
+                uint32_t lo, hi;
+                asm volatile("mad.lo.cc.u32 %0, %2, %3, %4;\n\t"
+                             "madc.hi.u32 %1, %2, %3, 0;"
+                             : "=&r"(lo), "=r"(hi)
+                             : "r"(a), "r"(x[k]), "r"(c[k]));
+                x[k] = lo;
+                c[k] = hi;
             } else if constexpr (OP == 1) {
-                x[k] = 69069u * x[k] + 1234567u;
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[k]) : "r"(69069u), "r"(c[k]));
             } else if constexpr (OP == 2) {
-                x[k] ^= x[k] << 13;
+                asm volatile("{\n\t.reg .b32 t;\n\tshl.b32 t, %0, 13;\n\txor.b32 %0, %0, t;\n\t}"
+                             : "+r"(x[k]));
             } else {
-                x[k] += c[k];
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(x[k]) : "r"(c[k]));
             }
         }
     }
