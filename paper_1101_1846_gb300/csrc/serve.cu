@@ -215,7 +215,9 @@ int launch_tick(Server *S, int lane)
         rows = std::max<uint64_t>(1, std::min<uint64_t>(rows, share));
     }
     const uint64_t cap = rows * S->streams;
-    const uint32_t per_lane = (S->n_clients - lane + kLanes - 1) / kLanes;
+    // clients lane, lane + kLanes, ... (none when the lane is past the last client)
+    const uint32_t per_lane =
+        (uint32_t)lane < S->n_clients ? (S->n_clients - lane + kLanes - 1) / kLanes : 0;
     for (uint32_t k = 0; k < per_lane; ++k) {
         const uint32_t c = lane + kLanes * ((S->rr[lane] + k) % per_lane);
         if (S->active[c].empty())
