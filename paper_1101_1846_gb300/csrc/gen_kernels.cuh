@@ -150,17 +150,27 @@ gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
         *cnt = 0;
     }
     if (y > 0) {
+        // MWC32 / KISS: the tabulated a^(y*rows) when the handle's table is
+        // passed, else powering (calls captured in a CUDA graph)
+        bool mwc_done = false;
         if constexpr (KIND == RNG_MWC32 || KIND == RNG_KISS) {
-            const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0));
-            const uint4 hi =
-                __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0 + 2));
-            const uint64_t A[4] = {(uint64_t)lo.y << 32 | lo.x, (uint64_t)lo.w << 32 | lo.z,
-                                   (uint64_t)hi.y << 32 | hi.x, (uint64_t)hi.w << 32 | hi.z};
+            if (jmul) {
+                const uint4 lo =
+                    __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0));
+                const uint4 hi =
+                    __ldg(reinterpret_cast<const uint4 *>(jmul + (uint64_t)y * n + s0 + 2));
+                const uint64_t A[4] = {(uint64_t)lo.y << 32 | lo.x, (uint64_t)lo.w << 32 | lo.z,
+                                       (uint64_t)hi.y << 32 | hi.x, (uint64_t)hi.w << 32 | hi.z};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                mwc_apply(A[i], a[i], w[0][i], w[1][i]);
+                for (int i = 0; i < 4; ++i)
+                    mwc_apply(A[i], a[i], w[0][i], w[1][i]);
+                mwc_done = true;
+            }
         }
-        jump_streams<KIND, 4, KIND == RNG_MWC32 || KIND == RNG_KISS>(w, a, first, T);
+        if (mwc_done)
+            jump_streams<KIND, 4, true>(w, a, first, T);
+        else
+            jump_streams<KIND, 4, false>(w, a, first, T);
     }
     uint32_t *row = out + (uint64_t)first * ld + c_first;
     if constexpr (SYNC) {
@@ -271,7 +281,12 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
         JumpTables T{};
         const uint64_t *jmul = nullptr;
         int e = needs_jump_tables(KIND) ? jump_tables(&T) : RNG_OK;
-        if (!e && mont_table(KIND))
+        // Inside a CUDA graph capture the table is not (re)built: its kernel
+        // would only run at replay while later direct calls took it as ready.
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (!e)
+            e = cuda_status(cudaStreamIsCapturing(st, &cap));
+        if (!e && mont_table(KIND) && cap == cudaStreamCaptureStatusNone)
             e = mwc_jump_table(g, L, st, &jmul);
         if (e)
             return e;

@@ -84,8 +84,9 @@ reduce_kernel(rng_device_view v, uint64_t steps, uint64_t rows, uint64_t *__rest
     }
     const uint64_t first = (uint64_t)blockIdx.y * rows;
     const uint64_t mine = steps - first < rows ? steps - first : rows;
-    const uint64_t A =
-        ((KIND == RNG_MWC32 || KIND == RNG_KISS) && blockIdx.y > 0) ? jmul[blockIdx.y * n + s] : 0;
+    const uint64_t A = ((KIND == RNG_MWC32 || KIND == RNG_KISS) && blockIdx.y > 0 && jmul)
+                           ? jmul[blockIdx.y * n + s]
+                           : 0;
     jump_engine<KIND>(e, first, T, A);
     atomicAdd(reinterpret_cast<unsigned long long *>(out + s),
               (unsigned long long)consume<OP>(e, mine));
@@ -159,7 +160,11 @@ extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, 
     int status = RNG_OK;
     if (split && needs_jump_tables(g->kind))
         status = jump_tables(&T);
-    if (!status && split && mont_table(g->kind))
+    // no table build inside a CUDA graph capture (see gen_kernels.cuh)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!status && split)
+        status = cuda_status(cudaStreamIsCapturing(st, &cap));
+    if (!status && split && mont_table(g->kind) && cap == cudaStreamCaptureStatusNone)
         status = mwc_jump_table(g, rows, st, &jmul);
     if (!status && split)
         status = cuda_status(cudaMemsetAsync(o, 0, g->n * 8, st));

@@ -237,3 +237,31 @@ def test_device_view_describes_the_handle():
     x = Generator(oracle.XOR128, 40, 2).device_view()
     assert x.mult is None and x.state_words == 4
     g.close()
+
+
+@pytest.mark.parametrize("kind", [oracle.MWC, oracle.KISS])
+def test_split_calls_captured_in_a_cuda_graph(kind):
+    """A split call captured in a CUDA graph powers its jumps itself (the
+    handle's multiplier table is not built during a capture), so a direct
+    call made before the first replay, with another segment length, and the
+    replays all continue the one sequence."""
+    n, seed = 64, 23
+    g = Generator(kind, n, seed)
+    out = torch.empty((4096, n), dtype=torch.int32, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(graph, stream=side):
+        g.generate(4096, oracle.U32, out=out)
+    first = bits(g.generate(2048))          # not captured; another segment length
+    graph.replay()
+    second = bits(out)
+    graph.replay()
+    third = bits(out)
+    exp, st = oracle.generate(kind, oracle_a(kind, n), seeded(kind, n, seed), 2048 + 2 * 4096,
+                              oracle.U32)
+    assert np.array_equal(first, exp[:2048])
+    assert np.array_equal(second, exp[2048:6144])
+    assert np.array_equal(third, exp[6144:])
+    assert np.array_equal(gpu_state(g), st)
+    g.close()
