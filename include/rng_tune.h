@@ -18,7 +18,9 @@ extern "C" {
 /* Launch shape of the vector-store generate kernel for (kind, fmt):
  * v = groups of four streams per thread (1 or 2), block = threads per CTA
  * (power of two, 32..512), hint = 1 for streaming (evict-first) stores,
- * 0 for default stores.  Applies to later rng_generate calls in this process
+ * 0 for default stores, 2 for rows staged in shared memory and written by
+ * TMA bulk copies (32-byte aligned rows only; v and block then unused:
+ * CTAs of 256 threads, 1024 streams each).  Applies to later rng_generate calls in this process
  * on every device; does not change any output.  Returns 0 or RNG_ERR_ARG. */
 int gbrng_set_launch(int kind, int fmt, int v, int block, int hint);
 int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);

@@ -212,6 +212,82 @@ gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
     }
 }
 
+// Rows 32-byte aligned, outputs staged in shared memory and written by the
+// TMA engine (bulk asynchronous copies, shared -> global): a CTA of
+// kTmaThreads threads owns 4 * kTmaThreads consecutive streams (one group
+// of four per thread), generates kTmaRows rows at a time into one of two
+// shared buffers, and one thread writes each row's segment (4 KB for 1024
+// streams) with one bulk copy.  A buffer is refilled only after its
+// copies have finished reading it (wait_group.read), and the kernel waits
+// for every copy before it ends.  Threads past the last stream run the rows
+// with the others (the barriers are CTA-wide) and their words are not
+// copied.
+constexpr int kTmaThreads = 256;
+constexpr int kTmaRows = 4;
+
+__device__ __forceinline__ void tma_store_row(uint32_t *gdst, const uint32_t *ssrc,
+                                              uint32_t bytes)
+{
+    const uint32_t saddr = static_cast<uint32_t>(__cvta_generic_to_shared(ssrc));
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 :
+                 : "l"(gdst), "r"(saddr), "r"(bytes)
+                 : "memory");
+}
+
+template <int KIND, int FMT>
+__global__ void __launch_bounds__(kTmaThreads)
+gen_tma(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
+        uint32_t steps, uint32_t *__restrict__ out, uint64_t ld, uint64_t s_begin,
+        uint64_t count)
+{
+    __shared__ __align__(128) uint32_t buf[2][kTmaRows][4 * kTmaThreads];
+    constexpr int W = KindTraits<KIND>::W;
+    const uint64_t c0 = (uint64_t)blockIdx.x * 4 * kTmaThreads;  // CTA's first stream
+    const uint64_t c_first = c0 + 4 * (uint64_t)threadIdx.x;
+    const bool live = c_first < count;
+    const uint32_t bytes = (uint32_t)(4 * min((uint64_t)4 * kTmaThreads, count - c0));
+    const uint64_t s0 = s_begin + c_first;
+    uint32_t w[kMaxWords][4] = {};
+    uint32_t a[4] = {};
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            load4(state + k * n + s0, w[k]);
+        if constexpr (KindTraits<KIND>::MULT)
+            load4(mult + s0, a);
+    }
+    const bool leader = threadIdx.x == 0;
+    uint32_t row0 = 0;
+    for (int b = 0; row0 < steps; b ^= 1, row0 += kTmaRows) {
+        const uint32_t rows = min((uint32_t)kTmaRows, steps - row0);
+        if (leader)  // the copies that read this buffer two blocks ago are done
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncthreads();
+        for (uint32_t r = 0; r < rows; ++r) {
+            const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
+            const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
+            const uint32_t o2 = step_enc<KIND, FMT>(w, a, 2);
+            const uint32_t o3 = step_enc<KIND, FMT>(w, a, 3);
+            *reinterpret_cast<uint4 *>(&buf[b][r][4 * threadIdx.x]) = make_uint4(o0, o1, o2, o3);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (leader) {
+            for (uint32_t r = 0; r < rows; ++r)
+                tma_store_row(out + (uint64_t)(row0 + r) * ld + c0, &buf[b][r][0], bytes);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+    }
+    if (leader)
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (live) {
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            save4(state + k * n + s0, w[k]);
+    }
+}
+
 constexpr int kSMs = 152;
 // CTA size of the kernels with row barriers: large CTAs leave fewer CTA
 // boundaries, where neighbouring CTAs that drift apart split sectors.
@@ -321,6 +397,14 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
                 return set_error(RNG_ERR_ARG);
             sync<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
                                                        p.s_begin, count);
+        } else if (aligned && sh.hint == 2) {
+            // outputs staged in shared memory, rows written by bulk copies
+            const uint64_t blocks = (count + 4 * kTmaThreads - 1) / (4 * kTmaThreads);
+            if (blocks > 0x7FFFFFFFull)
+                return set_error(RNG_ERR_ARG);
+            auto tma = fmt == RNG_F32 ? gen_tma<KIND, RNG_F32> : gen_tma<KIND, RNG_U32>;
+            tma<<<(unsigned)blocks, kTmaThreads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                          p.s_begin, count);
         } else if (aligned) {
             int threads = sh.block;
             uint64_t groups = count / 4;
