@@ -19,7 +19,8 @@ struct Shape {
 // MWC and xor128 uint32 write their rows through TMA bulk copies (hint 2):
 // 6 % and 1.4 % faster per launch on GB300 than 16-byte stores; the FP32
 // forms measured the same, and KISS and XORSHIFT8, whose steps cost more,
-// ran 4-40 % slower that way.
+// ran 4-40 % slower that way.  Per-warp bulk copies of 512 B (each warp
+// staging its own rows, no block barrier) were slower than both.
 Shape g_shape[kKinds][2] = {
     {{1, 256, 2}, {2, 256, 1}},  // MWC u32, f32
     {{1, 256, 2}, {1, 128, 1}},  // xor128

@@ -25,24 +25,25 @@ def _built():
 
 
 class tma_hint:
-    def __init__(self, kind, fmt):
-        self.kind, self.fmt = kind, fmt
+    def __init__(self, kind, fmt, hint):
+        self.kind, self.fmt, self.hint = kind, fmt, hint
         self.saved = [ctypes.c_int() for _ in range(3)]
 
     def __enter__(self):
         capi.check(capi.lib().gbrng_get_launch(self.kind, self.fmt,
                                                *[ctypes.byref(v) for v in self.saved]))
-        capi.check(capi.lib().gbrng_set_launch(self.kind, self.fmt, 1, 256, 2))
+        capi.check(capi.lib().gbrng_set_launch(self.kind, self.fmt, 1, 256, self.hint))
 
     def __exit__(self, *exc):
         capi.check(capi.lib().gbrng_set_launch(self.kind, self.fmt,
                                                *[v.value for v in self.saved]))
 
 
+@pytest.mark.parametrize("hint", [2])
 @pytest.mark.parametrize("kind", range(6))
 @pytest.mark.parametrize("fmt", [oracle.U32, oracle.F32])
 @pytest.mark.parametrize("n,steps", [(8, 5), (1032, 64), (4096, 7), (1 << 16, 33)])
-def test_tma_store_path_equals_oracle(kind, fmt, n, steps):
+def test_tma_store_path_equals_oracle(hint, kind, fmt, n, steps):
     if kind in (oracle.MWC16X2, oracle.KISS_XOR) and n > capi.RNG_MAX_STREAMS_MWC16:
         pytest.skip("beyond the pair count")
     seed = 50 + n
@@ -50,7 +51,7 @@ def test_tma_store_path_equals_oracle(kind, fmt, n, steps):
     st = oracle.seed_streams(kind, a, seed, np.arange(n))
     g = Generator(kind, n, seed)
     out = torch.full((steps + 1, n), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
-    with tma_hint(kind, fmt):
+    with tma_hint(kind, fmt, hint):
         for call in range(2):
             g.generate(steps, fmt, out=out)
             got = out.cpu().numpy().view(np.uint32)
