@@ -89,11 +89,24 @@ KERNEL_SOURCES = ("include/gbrng_device.cuh", "paper_1101_1846_gb300/csrc/gen_bo
                   "paper_1101_1846_gb300/csrc/generate.cu", "paper_1101_1846_gb300/csrc/gbrng.cuh")
 
 
-def kernel_source_hash() -> str:
-    """Hash of the files the generate kernels are compiled from."""
+def _code_only(text: str) -> str:
+    """Source text without // comments, trailing blanks and empty lines, so
+    that editing a comment does not look like a change of the kernels."""
+    lines = []
+    for line in text.splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            lines.append(line)
+    return "\n".join(lines)
+
+
+def kernel_source_hash(read=None) -> str:
+    """Hash of the code (comments aside) of the files the generate kernels
+    are compiled from."""
+    read = read or (lambda name: (ROOT / name).read_text())
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        h.update((ROOT / name).read_bytes())
+        h.update(_code_only(read(name)).encode())
     return h.hexdigest()[:16]
 
 
