@@ -477,6 +477,13 @@ int rng_server_stats(rng_server_handle s, uint64_t *out8);
  * rows per tick. */
 int rng_server_set_tick_bytes(rng_server_handle s, uint64_t bytes);
 
+/* Shape of the engine's persistent kernel, as rng_plan_create's `threads`
+ * (a power of two in [32, 512]; default 512) and `ctas_per_sm` (0 = as many
+ * as fit).  Synchronises the engine's streams if ticks have run; the next
+ * tick of each lane uses the new shape.  Output is the same for any shape.
+ * RNG_ERR_ARG outside those ranges. */
+int rng_server_set_plan_shape(rng_server_handle s, int threads, int ctas_per_sm);
+
 /* Waits for the engine's work and frees everything.  NULL is ignored. */
 void rng_server_destroy(rng_server_handle s);
 

@@ -109,6 +109,7 @@ SIGNATURES = {
     "rng_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "rng_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "rng_server_set_tick_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "rng_server_set_plan_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "rng_server_destroy": (None, [ctypes.c_void_p]),
     "rng_last_error": (ctypes.c_int, []),
     "rng_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -119,6 +119,7 @@ struct Server {
     cudaEvent_t t0 = nullptr;
     uint32_t rr[kLanes] = {};  // round-robin start, per lane
     uint64_t tick_bytes = 0;  // target output per tick (0: chunk_rows alone)
+    int plan_threads = kServeThreads, plan_ctas = 0;  // persistent kernel shape
     uint64_t next_id = 0, n_admitted = 0, n_completed = 0, n_ticks = 0, samples = 0;
 };
 
@@ -240,7 +241,8 @@ int launch_tick(Server *S, int lane)
         return RNG_OK;
     int st;
     if (!S->plan[lane]) {
-        S->plan[lane] = rng_plan_create(S->items.data(), S->items.size(), kServeThreads, 0);
+        S->plan[lane] = rng_plan_create(S->items.data(), S->items.size(), S->plan_threads,
+                                        S->plan_ctas);
         st = S->plan[lane] ? RNG_OK : rng_last_error();
     } else {
         st = rng_plan_refill(S->plan[lane], S->items.data(), S->items.size(), S->stream[lane]);
@@ -583,6 +585,29 @@ extern "C" int rng_server_set_tick_bytes(rng_server_handle h, uint64_t bytes)
     if (!S)
         return set_error(RNG_ERR_ARG);
     S->tick_bytes = bytes;
+    return RNG_OK;
+}
+
+extern "C" int rng_server_set_plan_shape(rng_server_handle h, int threads, int ctas_per_sm)
+{
+    Server *S = reinterpret_cast<Server *>(h);
+    if (!S || threads < 32 || threads > 512 || (threads & (threads - 1)) || ctas_per_sm < 0 ||
+        ctas_per_sm > 32)
+        return set_error(RNG_ERR_ARG);
+    DeviceScope ds(S->device);
+    // the lanes' plans are rebuilt with the new shape at their next tick;
+    // wait for the ticks that still read them
+    for (int ln = 0; ln < kLanes; ++ln) {
+        if (!S->plan[ln])
+            continue;
+        int st = cuda_status(cudaStreamSynchronize(S->stream[ln]));
+        if (st)
+            return st;
+        rng_plan_destroy(S->plan[ln]);
+        S->plan[ln] = nullptr;
+    }
+    S->plan_threads = threads;
+    S->plan_ctas = ctas_per_sm;
     return RNG_OK;
 }
 

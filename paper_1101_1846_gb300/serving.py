@@ -17,7 +17,8 @@ from . import capi
 class Server:
     def __init__(self, kind: int = capi.RNG_KISS, n_clients: int = 256,
                  streams_per_client: int = 65536, seed_base: int = 0,
-                 budget_bytes: int = 40 << 30, chunk_rows: int = 64, tick_bytes: int = 0):
+                 budget_bytes: int = 40 << 30, chunk_rows: int = 64, tick_bytes: int = 0,
+                 plan_shape: tuple[int, int] | None = None):
         h = capi.lib().rng_server_create(kind, n_clients, streams_per_client, seed_base,
                                          budget_bytes, chunk_rows)
         if not h:
@@ -25,6 +26,9 @@ class Server:
         self.h = h
         if tick_bytes:
             capi.check(capi.lib().rng_server_set_tick_bytes(h, tick_bytes))
+        if plan_shape is not None:
+            capi.check(capi.lib().rng_server_set_plan_shape(h, *plan_shape),
+                       "rng_server_set_plan_shape")
         self.kind, self.n_clients, self.streams = kind, n_clients, streams_per_client
         self.seed_base = seed_base
         self._ids = (ctypes.c_uint64 * 4096)()

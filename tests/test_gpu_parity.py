@@ -384,6 +384,44 @@ def test_batch_equals_plain_and_oracle(threads):
     plan.close()
 
 
+@pytest.mark.parametrize("threads", [32, 128])
+def test_batch_many_tails(threads):
+    """Many tail tiles (the n % 4 last streams of an item) of mixed lengths,
+    tails-only items (fewer than four streams) and the tails of stream
+    subranges of one handle, all equal to plain calls."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    ins = []
+    for k in range(150):
+        kind, fmt = (oracle.KISS, 0) if k < 100 else (oracle.MWC, 1)
+        n = int(rng.choice([1, 2, 3, 5, 6, 7, 9, 13, 30, 61, 203]))
+        ins.append(workloads.Instance(kind, n, int(rng.integers(1, 200)), fmt, 500 + k))
+    gb, ob = _make(ins, offset_every=5)
+    gp, op = _make(ins, offset_every=5)
+    plan = Plan([BatchItem(g, i.n_per_stream, o, i.fmt) for g, i, o in zip(gb, ins, ob)],
+                threads=threads)
+    plan.launch()
+    for g, i, o in zip(gp, ins, op):
+        g.generate(i.n_per_stream, i.fmt, out=o)
+    torch.cuda.synchronize()
+    for k in range(len(ins)):
+        assert torch.equal(ob[k], op[k]), k
+        assert torch.equal(gb[k].get_state(), gp[k].get_state()), k
+    plan.close()
+    # subranges of one handle, each with a tail
+    n, steps = 203, 37
+    g1, g2 = Generator(oracle.XOR128, n, 4), Generator(oracle.XOR128, n, 4)
+    cuts = [0, 7, 18, 45, 46, 101, 150, 203]
+    o1 = torch.zeros(n * steps, dtype=torch.int32, device="cuda")
+    o2 = torch.zeros(n * steps, dtype=torch.int32, device="cuda")
+    items = [BatchItem(g1, steps, o1[a:], 0, s_begin=a, s_end=b, ld=n)
+             for a, b in zip(cuts, cuts[1:])]
+    Plan(items, threads=threads).launch()
+    g2.generate(steps, 0, out=o2)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    assert torch.equal(g1.get_state(), g2.get_state())
+
+
 def test_batch_graph_replay_continues_streams():
     ins = small_instances(20, seed=3)
     gb, ob = _make(ins)

@@ -110,6 +110,24 @@ def test_other_kinds_equal_oracle(kind):
     s.close()
 
 
+def test_plan_shape_keeps_outputs():
+    """Another kernel shape, set before the first tick and changed between
+    two halves of the log (the lanes' plans are rebuilt), gives the oracle's
+    outputs; invalid shapes are refused."""
+    n, clients = 1024, 4
+    log = make_log(40, clients, 30000, seed=21)
+    s = Server(capi.RNG_KISS, clients, n, seed_base=9, budget_bytes=64 << 20, chunk_rows=4,
+               plan_shape=(128, 2))
+    outs = run_all(s, log[:20])
+    capi.check(capi.lib().rng_server_set_plan_shape(s.h, 256, 0))
+    outs2 = run_all(s, log[20:])
+    outs.update({20 + i: v for i, v in outs2.items()})
+    check_against_oracle(s, log, outs, oracle.KISS, n)
+    for bad in ((0, 0), (96, 0), (1024, 0), (256, -1), (256, 33)):
+        assert capi.lib().rng_server_set_plan_shape(s.h, *bad) == capi.RNG_ERR_ARG
+    s.close()
+
+
 def test_admission_waits_for_budget():
     n, clients = 512, 2
     state = clients * n * 20
