@@ -401,6 +401,13 @@ def run_ours(args):
             "per_kernel": per_kernel, "write_only_probe_gbs": write_only_gbs,
         }
         line.update(extras)
+        # the batched and saturating serving rates against this run's
+        # single-instance full-device rate
+        if "batched" in line:
+            line["batched"]["over_plain_full_device"] = line["batched"]["value"] / value
+        sat = line.get("serving", {}).get("saturating")
+        if sat:
+            sat["over_plain_full_device"] = sat["gsamples_s"] / value
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -906,7 +913,6 @@ def run_extras(args, clock_mhz: float = 2070.0):
             "batched_ms", "gpu_launches")
     b = run_batched(args)  # the library's default plan shape (--tune to sweep shapes)
     extras["batched"] = {k: b[k] for k in keep if k in b}
-    extras["batched"]["over_plain_full_device"] = None
     s = run_serving(args)
     extras["serving"] = {k: s[k] for k in ("value", "p50_ms", "p99_ms", "mean_ms", "requests",
                                            "offered_gsamples_s", "saturating", "probe_checks",
