@@ -6,7 +6,7 @@
 //   body_vec    4 adjacent streams per group, V groups per thread, one
 //               16-byte store per group per step; rows 32-byte aligned.
 //   body_vec_sync  the same with one group per thread and a barrier every
-//               four rows, for rows that are 16- but not 32-byte aligned.
+//               SYNC_ROWS rows, for rows that are 16- but not 32-byte aligned.
 //   body_shift  4 adjacent streams per thread for rows that are NOT 16-byte
 //               aligned (any n, out 4-byte aligned): each row is written with
 //               16-byte stores at the aligned positions, taking the words
@@ -24,18 +24,40 @@ namespace gbrng {
 // multiplier word (MULT: a multiplier, or a packed pair of 16-bit ones).
 template <int KIND>
 struct KindTraits;
+// W: state words per stream; MULT: a per-stream multiplier word; SYNC_ROWS:
+// rows between block barriers in the barrier-synced bodies (a multiple of
+// four).  Four keeps the warps closest; the two kinds whose steps cost most
+// run faster with eight on GB300 (the two-word kinds and KISS slower).
 template <>
-struct KindTraits<RNG_MWC32> { static constexpr int W = 2; static constexpr bool MULT = true; };
+struct KindTraits<RNG_MWC32> {
+    static constexpr int W = 2, SYNC_ROWS = 4;
+    static constexpr bool MULT = true;
+};
 template <>
-struct KindTraits<RNG_XOR128> { static constexpr int W = 4; static constexpr bool MULT = false; };
+struct KindTraits<RNG_XOR128> {
+    static constexpr int W = 4, SYNC_ROWS = 4;
+    static constexpr bool MULT = false;
+};
 template <>
-struct KindTraits<RNG_KISS> { static constexpr int W = 4; static constexpr bool MULT = true; };
+struct KindTraits<RNG_KISS> {
+    static constexpr int W = 4, SYNC_ROWS = 4;
+    static constexpr bool MULT = true;
+};
 template <>
-struct KindTraits<RNG_MWC16X2> { static constexpr int W = 2; static constexpr bool MULT = true; };
+struct KindTraits<RNG_MWC16X2> {
+    static constexpr int W = 2, SYNC_ROWS = 4;
+    static constexpr bool MULT = true;
+};
 template <>
-struct KindTraits<RNG_XORSHIFT8> { static constexpr int W = 8; static constexpr bool MULT = false; };
+struct KindTraits<RNG_XORSHIFT8> {
+    static constexpr int W = 8, SYNC_ROWS = 8;
+    static constexpr bool MULT = false;
+};
 template <>
-struct KindTraits<RNG_KISS_XOR> { static constexpr int W = 4; static constexpr bool MULT = true; };
+struct KindTraits<RNG_KISS_XOR> {
+    static constexpr int W = 4, SYNC_ROWS = 8;
+    static constexpr bool MULT = true;
+};
 
 // Register arrays hold up to kMaxWords words per stream; a kind touches only
 // its first W, and the unused entries cost no registers.
@@ -149,7 +171,7 @@ __device__ __forceinline__ void body_vec(uint32_t *__restrict__ state,
 
 // Aligned vector body for rows that are 16-byte but not 32-byte aligned
 // (n % 8 != 0 or a 32-byte misaligned output): one group of four streams per
-// thread, and a barrier every four rows.  A warp's 512-byte row window then
+// thread, and a barrier every SYNC_ROWS rows.  A warp's 512-byte row window then
 // begins or ends inside a 32-byte DRAM sector that its neighbour completes;
 // keeping the CTA's warps within a few rows of each other lets the two
 // halves meet in L2 instead of reaching DRAM as partial sectors (which cost a
@@ -173,8 +195,10 @@ __device__ __forceinline__ void body_vec_sync(uint32_t *__restrict__ state,
     }
     uint32_t *row = row0;
     const uint32_t blocks = steps / 4;
+    constexpr uint32_t every = KindTraits<KIND>::SYNC_ROWS / 4;  // blocks per barrier
     for (uint32_t b = 0; b < blocks; ++b) {
-        __syncthreads();
+        if (b % every == 0)
+            __syncthreads();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
@@ -268,8 +292,10 @@ __device__ __forceinline__ void shift_rows(uint32_t (&w)[kMaxWords][4], const ui
                                            bool owner, bool prev, bool next, bool lead,
                                            bool trail)
 {
+    constexpr uint32_t every = KindTraits<KIND>::SYNC_ROWS / 4;  // blocks per barrier
     for (uint32_t b = 0; b < blocks; ++b) {
-        __syncthreads();  // keep the CTA's warps within four rows of each other
+        if (b % every == 0)
+            __syncthreads();  // keep the CTA's warps within a few rows of each other
         shift_row<KIND, FMT, HINT, R0, EDGE>(w, a, row, owner, prev, next, lead, trail);
         row += ld;
         shift_row<KIND, FMT, HINT, (R0 + DR) & 3, EDGE>(w, a, row, owner, prev, next, lead,
@@ -332,8 +358,8 @@ __device__ __forceinline__ void shift_row_rt(uint32_t (&w)[kMaxWords][4], const 
 // row alignment, and a warp's halo lane writes the chunk that straddles the
 // warp boundary (shift_row); only the CTA's first lane and the owner of its
 // last group store stray words singly.  The barrier after the state loads
-// keeps every halo read ahead of the owner's write-back, and one every four
-// rows keeps the warps together (see body_vec_sync): every warp runs the
+// keeps every halo read ahead of the owner's write-back, and one every
+// SYNC_ROWS rows keeps the warps together (see body_vec_sync): every warp runs the
 // rows, idle lanes storing nothing.
 template <int KIND, int FMT, int HINT>
 __device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,

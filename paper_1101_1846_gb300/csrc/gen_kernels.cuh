@@ -54,7 +54,7 @@ gen_vec(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_
 }
 
 // Rows 16-byte but not 32-byte aligned: one group per thread, barriers every
-// four rows; every thread runs the rows (idle groups store nothing).
+// SYNC_ROWS rows; every thread runs the rows (idle groups store nothing).
 template <int KIND, int FMT, int HINT>
 __global__ void __launch_bounds__(512)
 gen_vec_sync(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint64_t n,
@@ -106,7 +106,7 @@ gen_shift(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
 // clears the counter for the next call.
 //
 // SYNC: rows 16- but not 32-byte aligned.  As in body_vec_sync, a barrier
-// every four rows keeps the CTA's warps together so that the two halves of
+// every SYNC_ROWS rows keeps the CTA's warps together so that the two halves of
 // a shared DRAM sector meet in L2; every thread of the CTA then runs the
 // rows (a CTA shares its segment, hence its jump and its row count), and
 // threads past the last group store nothing and count no arrival.
@@ -175,7 +175,7 @@ gen_split(uint32_t *__restrict__ state, const uint32_t *__restrict__ mult, uint6
     uint32_t *row = out + (uint64_t)first * ld + c_first;
     if constexpr (SYNC) {
         for (uint32_t j = 0; j < mine; ++j) {
-            if ((j & 3) == 0)
+            if (j % KindTraits<KIND>::SYNC_ROWS == 0)
                 __syncthreads();
             const uint32_t o0 = step_enc<KIND, FMT>(w, a, 0);
             const uint32_t o1 = step_enc<KIND, FMT>(w, a, 1);
