@@ -36,8 +36,15 @@ Shape g_shape[kKinds][2] = {
 // xor128 128-column products, the base-2^16 MWC parts a 64-bit powering
 // each; XORSHIFT8's 256-column products cost more than splitting gains.
 int g_split_log2[kKinds] = {6, 8, 7, 8, 0, 8};
-// Threads that fill the device (CTAs of 256 at full occupancy).
-constexpr uint64_t kFillThreads = (uint64_t)kSMs * 1024;
+// Calls of fewer threads than half of this are "few-stream" calls, which
+// split when their rows allow.
+constexpr uint64_t kFewStreamThreads = (uint64_t)kSMs * 1024;
+// Threads per SM a split generate call aims for, per kind.  MWC32 and KISS
+// (whose MWC jumps are tabulated per handle) and xor128 run best with 2048
+// (MWC32 76,632 x 16,384: 1584 GS/s with 1024, 1748 with 2048); the
+// base-2^16 kinds power every segment's jump, and KISS_XOR ran 7 % slower
+// with 2048.  Consumer (reduce) calls keep 1024.
+int g_split_fill[kKinds] = {2048, 2048, 2048, 1024, 1024, 1024};
 
 }  // namespace
 
@@ -47,22 +54,29 @@ LaunchShape launch_shape(int kind, int fmt)
     return LaunchShape{s.v, s.block, s.hint};
 }
 
-uint32_t split_max_segments(uint64_t n)
+uint64_t split_fill(int kind, bool reduce)
+{
+    return reduce ? kFewStreamThreads : (uint64_t)kSMs * g_split_fill[kind];
+}
+
+uint32_t split_max_segments(int kind, uint64_t n)
 {
     const uint64_t threads = (n + 3) / 4;
-    return (uint32_t)std::min<uint64_t>(kFillThreads / std::max<uint64_t>(threads, 1), 65535);
+    const uint64_t fill = std::max(split_fill(kind, false), split_fill(kind, true));
+    return (uint32_t)std::min<uint64_t>(fill / std::max<uint64_t>(threads, 1), 65535);
 }
 
 bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per_thread,
-                uint64_t max_segments, uint64_t *rows, uint64_t *segments)
+                uint64_t max_segments, uint64_t fill_threads, uint64_t *rows,
+                uint64_t *segments)
 {
     const int l0 = g_split_log2[kind];
     if (l0 == 0 || streams == 0 || streams > kSplitMaxStreams || steps > (1ull << 31))
         return false;
     const uint64_t threads = (streams + streams_per_thread - 1) / streams_per_thread;
-    if (2 * threads > kFillThreads)
+    if (2 * threads > kFewStreamThreads)
         return false;  // enough streams to fill the device already
-    const uint64_t want = std::min<uint64_t>(std::min<uint64_t>(kFillThreads / threads, 65535),
+    const uint64_t want = std::min<uint64_t>(std::min<uint64_t>(fill_threads / threads, 65535),
                                              max_segments);
     uint64_t L = 1ull << l0;
     while (L < steps && (steps + L - 1) / L > want)
