@@ -134,7 +134,7 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     // buffers of split calls (few streams only): the final-state stash, the
     // arrival counters (zero) and the MWC jump multipliers
     if (!st && n_streams <= kSplitMaxStreams) {
-        g->jmul_segs = split_max_segments(kind, n_streams);
+        g->jmul_segs = split_max_segments(n_streams);
         if (cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess ||
             cudaMalloc(&g->d_cnt, n_streams * 4) != cudaSuccess ||
             (mont_table(kind) &&

@@ -85,9 +85,9 @@ int launch_generate_paper(int kind, int fmt, const GenLaunch &p, cudaStream_t st
 bool split_plan(int kind, uint64_t streams, uint64_t steps, uint64_t streams_per_thread,
                 uint64_t max_segments, uint64_t fill_threads, uint64_t *rows,
                 uint64_t *segments);
-// Threads a split call of `kind` aims for: generate calls, or consumer
+// Threads a split call aims for: generate calls, or consumer
 // (rng_generate_reduce) calls.
-uint64_t split_fill(int kind, bool reduce);
+uint64_t split_fill(bool reduce);
 
 // jump.cu: device tables of the GF(2) and affine jumps, built on first use
 // on the current device (synchronises then).
@@ -103,8 +103,8 @@ int launch_jump(Gen *g, uint64_t k, cudaStream_t st);
 // The handle's MWC jump multipliers for segments of `rows` rows, rebuilt on
 // `st` when `rows` differs from the table's (MWC32 and KISS handles only).
 int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **table);
-// Most segments a split call on a handle of `kind` and n streams can have.
-uint32_t split_max_segments(int kind, uint64_t n);
+// Most segments a split call on a handle of n streams can have.
+uint32_t split_max_segments(uint64_t n);
 
 inline int words_of(int kind)
 {

@@ -353,7 +353,7 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
     uint64_t L = 0, S = 0;
     Gen *g = p.owner;
     if (g && g->d_split && aligned &&
-        split_plan(KIND, count, p.steps, 4, g->jmul_segs, split_fill(KIND, false), &L, &S)) {
+        split_plan(KIND, count, p.steps, 4, g->jmul_segs, split_fill(false), &L, &S)) {
         JumpTables T{};
         const uint64_t *jmul = nullptr;
         int e = needs_jump_tables(KIND) ? jump_tables(&T) : RNG_OK;

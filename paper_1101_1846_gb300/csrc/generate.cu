@@ -33,18 +33,19 @@ Shape g_shape[kKinds][2] = {
 // Fewest rows of a split segment, as log2, per kind (0: never split).  The
 // jump that starts a segment costs about as much as this many rows: MWC32 a
 // tabulated Montgomery product, KISS that plus 32-column GF(2) products,
-// xor128 128-column products, the base-2^16 MWC parts a 64-bit powering
-// each; XORSHIFT8's 256-column products cost more than splitting gains.
+// xor128 128-column products, the base-2^16 MWC parts a 32-bit Montgomery
+// powering each; XORSHIFT8's 256-column products cost more than splitting
+// gains.
 int g_split_log2[kKinds] = {6, 8, 7, 8, 0, 8};
 // Calls of fewer threads than half of this are "few-stream" calls, which
 // split when their rows allow.
 constexpr uint64_t kFewStreamThreads = (uint64_t)kSMs * 1024;
-// Threads per SM a split generate call aims for, per kind.  MWC32 and KISS
-// (whose MWC jumps are tabulated per handle) and xor128 run best with 2048
-// (MWC32 76,632 x 16,384: 1584 GS/s with 1024, 1748 with 2048); the
-// base-2^16 kinds power every segment's jump, and KISS_XOR ran 7 % slower
-// with 2048.  Consumer (reduce) calls keep 1024.
-int g_split_fill[kKinds] = {2048, 2048, 2048, 1024, 1024, 1024};
+// Threads a split generate call aims for: 2048 per SM, the most that can be
+// resident.  Against 1024 per SM this was measured on GB300 at
+// 76,632 x 16,384: MWC32 1584 -> 1740 GS/s, KISS 1575 -> 1680, xor128
+// 1575 -> 1670; at 76,636 x 16,384, MWC16X2 1449 -> 1500 and KISS_XOR
+// 1541 -> 1680.  Consumer (reduce) calls, one stream per thread, keep 1024.
+constexpr uint64_t kSplitFillThreads = (uint64_t)kSMs * 2048;
 
 }  // namespace
 
@@ -54,15 +55,15 @@ LaunchShape launch_shape(int kind, int fmt)
     return LaunchShape{s.v, s.block, s.hint};
 }
 
-uint64_t split_fill(int kind, bool reduce)
+uint64_t split_fill(bool reduce)
 {
-    return reduce ? kFewStreamThreads : (uint64_t)kSMs * g_split_fill[kind];
+    return reduce ? kFewStreamThreads : kSplitFillThreads;
 }
 
-uint32_t split_max_segments(int kind, uint64_t n)
+uint32_t split_max_segments(uint64_t n)
 {
     const uint64_t threads = (n + 3) / 4;
-    const uint64_t fill = std::max(split_fill(kind, false), split_fill(kind, true));
+    const uint64_t fill = std::max(split_fill(false), split_fill(true));
     return (uint32_t)std::min<uint64_t>(fill / std::max<uint64_t>(threads, 1), 65535);
 }
 

@@ -60,20 +60,25 @@ __device__ __forceinline__ void mwc_jump(uint32_t a, uint32_t &x, uint32_t &c, u
 
 // One base-2^16 part packed as z = x | c << 16, multiplier a < 2^16: k steps
 // multiply t = a x + c by a^k mod p (p = a 2^16 - 1); then x = t div a,
-// c = t mod a.
+// c = t mod a.  The power is taken in Montgomery form with R = 2^32, where
+// a is 2^16 (a 2^16 = 1 mod p, so a R = 2^16 mod p) and -p^-1 mod 2^32 is
+// 1 + a 2^16, so nothing needs a division; left to right from k's top bit.
 __device__ __forceinline__ void mwc16_jump(uint32_t a, uint32_t &z, uint64_t k)
 {
     if (k == 0)
         return;
-    const uint64_t p = ((uint64_t)a << 16) - 1;
-    uint64_t A = 1, b = a;
-    for (uint64_t e = k; e; e >>= 1) {
-        if (e & 1)
-            A = A * b % p;
-        b = b * b % p;
+    const uint32_t p = (a << 16) - 1u;
+    const uint32_t ninv = (a << 16) + 1u;
+    const uint32_t base = 1u << 16;  // a in Montgomery form
+    uint32_t A = base;
+    for (int bit = 62 - __clzll((long long)k); bit >= 0; --bit) {
+        A = mont_mul32(A, A, p, ninv);
+        if ((k >> bit) & 1u)
+            A = mont_mul32(A, base, p, ninv);
     }
-    const uint64_t t = A * ((uint64_t)a * (z & 0xFFFFu) + (z >> 16)) % p;
-    z = (uint32_t)(t / a) | ((uint32_t)(t % a) << 16);
+    // A = a^k R mod p; one more product with t (plain) gives a^k t mod p
+    const uint32_t t = mont_mul32(A, a * (z & 0xFFFFu) + (z >> 16), p, ninv);
+    z = (t / a) | ((t % a) << 16);
 }
 
 // v <- M v for a 128 x 128 GF(2) matrix given by columns (word w of column j

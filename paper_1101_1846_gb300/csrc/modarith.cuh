@@ -1,7 +1,7 @@
-// 64-bit modular arithmetic on the device: Montgomery multiplication with
-// R = 2^64 (Montgomery, "Modular multiplication without trial division",
-// Math. Comp. 44, 1985).  Used by the multiplier search (Miller-Rabin) and
-// by the MWC jump-ahead.
+// Modular arithmetic on the device: Montgomery multiplication with R = 2^64
+// and R = 2^32 (Montgomery, "Modular multiplication without trial
+// division", Math. Comp. 44, 1985).  Used by the multiplier search
+// (Miller-Rabin) and by the MWC jump-ahead.
 #pragma once
 
 #include <stdint.h>
@@ -23,6 +23,16 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t n,
     if (over || s2 >= n)
         s2 -= n;  // true sum is < 2n, so one subtraction suffices
     return s2;
+}
+
+// a * b * 2^-32 mod n for a, b < n < 2^32, n odd; ninv = -n^-1 mod 2^32.
+__device__ __forceinline__ uint32_t mont_mul32(uint32_t a, uint32_t b, uint32_t n, uint32_t ninv)
+{
+    const uint64_t t = (uint64_t)a * b;
+    const uint32_t m = (uint32_t)t * ninv;
+    const uint64_t s = t + (uint64_t)m * n;  // divisible by 2^32; true sum < 2^65
+    const uint64_t r = (s >> 32) | ((uint64_t)(s < t) << 32);  // < 2n
+    return (uint32_t)(r >= n ? r - n : r);
 }
 
 }  // namespace gbrng

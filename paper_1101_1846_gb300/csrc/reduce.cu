@@ -150,7 +150,7 @@ extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, 
     // pairs never straddle segments: split rows are powers of two >= 2
     const bool split = g->d_split &&
                        split_plan(g->kind, g->n, n_per_stream, 1, g->jmul_segs,
-                                  split_fill(g->kind, true), &rows, &segs);
+                                  split_fill(true), &rows, &segs);
     if (!split) {
         rows = n_per_stream;
         segs = 1;
