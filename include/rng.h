@@ -327,7 +327,9 @@ typedef struct rng_plan *rng_plan_handle;
  * counts, lengths and formats: the streams of every item are cut into tiles
  * of 4 * threads streams when its rows are 16-byte aligned, else of
  * 4 * (31 * threads / 32 + 1) streams (the last (s_end - s_begin) % 4
- * streams of such an item form a tile of their own), the tiles are ordered by length, largest first, and
+ * streams of such an item run in the last warp of its last tile when that
+ * warp holds no group, else in a tile of their own), the tiles are ordered
+ * by length, largest first, and
  * the work list is copied to the device (synchronises).  threads = CTA size (power of two, 32..512; 0 = 512),
  * ctas_per_sm = resident CTAs the persistent grid puts on each SM (1..32;
  * 0 = as many as fit).  Items of the same handle must cover disjoint stream
@@ -498,7 +500,7 @@ void rng_server_destroy(rng_server_handle s);
  * until the process exits): a call may cover at most 4096 items and 32768
  * tiles (an item of c = s_end - s_begin streams takes ceil(c / 512) tiles
  * when its rows are 16-byte aligned, else ceil((c - c % 4) / 500) tiles plus
- * one when c % 4 != 0); more returns RNG_ERR_ARG and launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
+ * at most one when c % 4 != 0); more returns RNG_ERR_ARG and launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
  * called.  The first call on a device looks up the device address of that
  * array (once per device), so make the first call before any stream capture.
  * Asynchronous on `cuda_stream`: the work list is copied from library host

@@ -12,7 +12,9 @@
 //            with row barriers unless every row is 32-byte aligned;
 //   shifted  (otherwise) the first n & ~3 streams, 4*(31*threads/32 + 1)
 //            per tile, rows realigned by warp shuffles;
-//   tail     the last n % 4 streams, one tile, one stream per thread.
+//   tail     the last n % 4 streams, one stream per thread: run by the last
+//            warp of the item's last realigned tile when that warp holds no
+//            group (most items), else as a tile of its own.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -36,7 +38,7 @@ struct Unit {
     uint32_t s0;         // first stream of the tile
     uint32_t count;      // streams in the tile
     uint32_t code;       // kind | fmt << 2 | mode << 3
-    uint32_t pad;
+    uint32_t tail;       // shifted tiles: tail streams after the tile's (0-3)
 };
 
 template <int KIND, int FMT, int HINT>
@@ -53,7 +55,16 @@ __device__ __forceinline__ void run_unit(const Unit &u)
         body_vec_sync<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c_first, u.ld,
                                        u.s0 + c_first, c_first < u.count);
     } else if (mode == kShifted) {
-        body_shift<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out, u.ld, u.s0, u.count / 4);
+        // tail streams u.s0 + count .. + tail: the last warp, which then
+        // holds no group (fill_units checks), with the same barriers
+        const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (u.tail && warp == (blockDim.x >> 5) - 1)
+            body_scalar_sync<KIND, FMT, HINT>(u.state, u.a, u.n, steps,
+                                              u.out + u.count + lane, u.ld,
+                                              u.s0 + u.count + lane, lane < u.tail);
+        else
+            body_shift<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out, u.ld, u.s0,
+                                        u.count / 4);
     } else {
         const uint64_t c = threadIdx.x;
         if (c < u.count)
@@ -185,8 +196,18 @@ uint64_t fill_units(const rng_batch_item *items, size_t n_items, int threads, Un
         };
         for (uint64_t c0 = 0; c0 < main; c0 += tile)
             put(c0, std::min<uint64_t>(tile, main - c0), aligned ? amode : kShifted);
-        if (main < n_item)
+        // the tail joins the last realigned tile when that tile's last warp
+        // holds no group (at most 31 (K - 1) groups: warp K - 2's halo lane
+        // then holds no live group either)
+        const uint64_t last = main % tile ? main % tile : tile;
+        const bool join = !aligned && main > 0 && main < n_item &&
+                          last / 4 <= 31ull * (threads / 32 - 1);
+        if (join) {
+            if (out && count - 1 < cap)
+                out[count - 1].tail = (uint32_t)(n_item - main);
+        } else if (main < n_item) {
             put(main, n_item - main, kTail);
+        }
     }
     return count;
 }
