@@ -426,56 +426,6 @@ __device__ __forceinline__ void body_shift(uint32_t *__restrict__ state,
     }
 }
 
-// The scalar body with body_shift's barriers (one after the state loads,
-// then one every SYNC_ROWS rows of the blocks of four), so that one warp of a
-// realigned CTA can run the n % 4 tail streams beside the other warps'
-// groups: the tail's words share DRAM sectors with the CTA's last chunk and
-// reach L2 with it.  Threads that are not `live` step zero state and store
-// nothing; every thread of the warp must call this.
-template <int KIND, int FMT, int HINT>
-__device__ __forceinline__ void body_scalar_sync(uint32_t *__restrict__ state,
-                                                 const uint32_t *__restrict__ mult, uint64_t n,
-                                                 uint32_t steps, uint32_t *__restrict__ p0,
-                                                 uint64_t ld, uint64_t s, bool live)
-{
-    constexpr int W = KindTraits<KIND>::W;
-    uint32_t w[kMaxWords][4] = {};
-    uint32_t a[4] = {0, 0, 0, 0};
-    if (live) {
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            w[k][0] = state[k * n + s];
-        if constexpr (KindTraits<KIND>::MULT)
-            a[0] = mult[s];
-    }
-    __syncthreads();  // body_shift's barrier after its state loads
-    constexpr uint32_t every = KindTraits<KIND>::SYNC_ROWS / 4;
-    const uint32_t blocks = steps / 4;
-    uint32_t *p = p0;
-    for (uint32_t b = 0; b < blocks; ++b) {
-        if (b % every == 0)
-            __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
-            if (live)
-                store4<HINT>(p, o);
-            p += ld;
-        }
-    }
-    for (uint32_t j = 4 * blocks; j < steps; ++j) {
-        const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
-        if (live)
-            store4<HINT>(p, o);
-        p += ld;
-    }
-    if (live) {
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            state[k * n + s] = w[k][0];
-    }
-}
-
 // Scalar body: one stream s (< n), 4-byte stores from p0 (its element in
 // row 0); any n, 4-byte aligned output.
 template <int KIND, int FMT, int HINT>
