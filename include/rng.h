@@ -158,9 +158,14 @@ int rng_generate(rng_handle h, uint64_t n_per_stream, void *out, int fmt);
  * outputs into segments of 2^l rows (l chosen per kind; gbrng_set_split),
  * starts every segment from the state jumped ahead to it (rng_jump) and
  * runs the segments side by side; the final state goes through a scratch
- * buffer allocated with the handle on first use (RNG_ERR_OOM if that
- * fails).  The outputs and the state are those of the plain sequence
- * (sequence splitting, Sec. "Parallelizing RNGs"). */
+ * buffer allocated with the handle.  For MWC32 and KISS the segments' MWC
+ * jumps come from a per-handle table of multipliers (8 bytes per stream and
+ * segment), allocated by the first split call that needs it and grown when
+ * a call needs more segments: that call synchronises the device and returns
+ * RNG_ERR_OOM if the allocation fails.  A split call captured in a CUDA
+ * graph never allocates; it powers the multipliers in the kernel instead.
+ * The outputs and the state are those of the plain sequence (sequence
+ * splitting, Sec. "Parallelizing RNGs"). */
 
 /* Advances only streams [s_begin, s_end) (0 <= s_begin < s_end <= n_streams)
  * n_per_stream times; the other streams keep their state.  Output j of

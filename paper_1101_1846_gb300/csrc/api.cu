@@ -136,9 +136,7 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     if (!st && n_streams <= kSplitMaxStreams) {
         g->jmul_segs = split_max_segments(n_streams);
         if (cudaMalloc(&g->d_split, (size_t)g->words * n_streams * 4) != cudaSuccess ||
-            cudaMalloc(&g->d_cnt, n_streams * 4) != cudaSuccess ||
-            (mont_table(kind) &&
-             cudaMalloc(&g->d_jmul, (size_t)g->jmul_segs * n_streams * 8) != cudaSuccess))
+            cudaMalloc(&g->d_cnt, n_streams * 4) != cudaSuccess)
             st = set_error(RNG_ERR_OOM);
         else
             st = cuda_status(cudaMemset(g->d_cnt, 0, n_streams * 4));

@@ -29,9 +29,11 @@ struct Gen {
     uint32_t *d_split = nullptr;  // final state stash, same layout as d_state
     uint32_t *d_cnt = nullptr;    // arrival counters, n entries, zero between calls
     uint64_t *d_jmul = nullptr;   // MWC jump multipliers: a^(y*jmul_rows) mod p in
-                                  // Montgomery form at d_jmul[y*n + s], y < jmul_segs
+                                  // Montgomery form at d_jmul[y*n + s], y < jmul_cap;
+                                  // allocated by the first split call that needs it
     uint64_t jmul_rows = 0;       // rows per segment the table was built for (0: none)
-    uint32_t jmul_segs = 0;       // segments the table holds
+    uint32_t jmul_cap = 0;        // segments the table holds
+    uint32_t jmul_segs = 0;       // most segments a split call of this handle has
     // staging for rng_generate_host
     void *d_stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
@@ -100,9 +102,12 @@ struct JumpTables {
 };
 int jump_tables(JumpTables *t);
 int launch_jump(Gen *g, uint64_t k, cudaStream_t st);
-// The handle's MWC jump multipliers for segments of `rows` rows, rebuilt on
-// `st` when `rows` differs from the table's (MWC32 and KISS handles only).
-int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **table);
+// The handle's MWC jump multipliers for `segs` segments of `rows` rows,
+// rebuilt on `st` when `rows` differs from the table's (MWC32 and KISS
+// handles only).  The table is allocated, or grown, when a call needs more
+// segments than it holds (synchronises then; never inside a capture).
+int mwc_jump_table(Gen *g, uint64_t rows, uint64_t segs, cudaStream_t st,
+                   const uint64_t **table);
 // Most segments a split call on a handle of n streams can have.
 uint32_t split_max_segments(uint64_t n);
 

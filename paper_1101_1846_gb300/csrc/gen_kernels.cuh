@@ -363,7 +363,7 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
         if (!e)
             e = cuda_status(cudaStreamIsCapturing(st, &cap));
         if (!e && mont_table(KIND) && cap == cudaStreamCaptureStatusNone)
-            e = mwc_jump_table(g, L, st, &jmul);
+            e = mwc_jump_table(g, L, S, st, &jmul);
         if (e)
             return e;
         using SplitFn = void (*)(uint32_t *, const uint32_t *, uint64_t, uint32_t, uint32_t,

@@ -190,14 +190,29 @@ int jump_tables(JumpTables *out)
     return RNG_OK;
 }
 
-int mwc_jump_table(Gen *g, uint64_t rows, cudaStream_t st, const uint64_t **table)
+int mwc_jump_table(Gen *g, uint64_t rows, uint64_t segs, cudaStream_t st,
+                   const uint64_t **table)
 {
-    if (!g->d_jmul || !g->d_a)
+    if (!g->d_a || segs == 0 || segs > g->jmul_segs)
         return set_error(RNG_ERR_ARG);
+    if (segs > g->jmul_cap) {
+        // grow: the old table may still be read by earlier calls (on any
+        // stream), so wait for the device before freeing it
+        int e = cuda_status(cudaDeviceSynchronize());
+        if (e)
+            return e;
+        cudaFree(g->d_jmul);
+        g->d_jmul = nullptr;
+        g->jmul_cap = 0;
+        g->jmul_rows = 0;
+        if (cudaMalloc(&g->d_jmul, (size_t)segs * g->n * 8) != cudaSuccess)
+            return set_error(RNG_ERR_OOM);
+        g->jmul_cap = (uint32_t)segs;
+    }
     if (g->jmul_rows != rows) {
-        const uint64_t total = g->n * g->jmul_segs;
+        const uint64_t total = g->n * g->jmul_cap;
         const uint64_t blocks = (total + 255) / 256;
-        mwc_table_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->d_a, g->n, rows, g->jmul_segs,
+        mwc_table_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->d_a, g->n, rows, g->jmul_cap,
                                                            g->d_jmul);
         int e = cuda_status(cudaGetLastError());
         if (e)

@@ -166,7 +166,7 @@ extern "C" int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, 
     if (!status && split)
         status = cuda_status(cudaStreamIsCapturing(st, &cap));
     if (!status && split && mont_table(g->kind) && cap == cudaStreamCaptureStatusNone)
-        status = mwc_jump_table(g, rows, st, &jmul);
+        status = mwc_jump_table(g, rows, segs, st, &jmul);
     if (!status && split)
         status = cuda_status(cudaMemsetAsync(o, 0, g->n * 8, st));
     if (!status) {
