@@ -186,6 +186,40 @@ def test_split_generate_equals_oracle(kind, n, steps, fmt):
     g.close()
 
 
+@pytest.mark.parametrize("kind", [oracle.MWC, oracle.KISS])
+def test_split_jump_table_grows_and_rebuilds(kind):
+    """One handle through split calls whose segment counts and lengths
+    change: the per-handle MWC jump table is allocated by the first, grown
+    when a call needs more segments, and rebuilt when the segment length
+    changes; consumer calls share it.  Every output and state equals the
+    oracle's."""
+    n, seed = 64, 29
+    g = Generator(kind, n, seed)
+    a = oracle_a(kind, n)
+    st = seeded(kind, n, seed)
+    # a few segments (allocates), many (grows), then longer segments
+    # (rebuilds); the consumer calls go back to the default length (rebuild)
+    # and then need more segments again (grow)
+    for steps, log2_rows in ((300, None), (6000, None), (700, 8)):
+        if log2_rows is None:
+            got = bits(g.generate(steps))
+        else:
+            with split_set(kind, log2_rows):
+                got = bits(g.generate(steps))
+        exp, st = oracle.generate(kind, a, st, steps, oracle.U32)
+        assert np.array_equal(got, exp), steps
+        assert np.array_equal(gpu_state(g), st), steps
+    for steps in (2500, 12000):
+        got = u64(g.generate_reduce(steps, oracle.SUM_U32))
+        exp, st = oracle.reduce(kind, a, st, steps, oracle.SUM_U32)
+        assert np.array_equal(got, exp), steps
+        assert np.array_equal(gpu_state(g), st), steps
+    got = bits(g.generate(4000))
+    exp, st = oracle.generate(kind, a, st, 4000, oracle.U32)
+    assert np.array_equal(got, exp)
+    g.close()
+
+
 def test_split_mwc_4096_by_4096_equals_oracle():
     """The few-streams configuration: MWC, 4096 streams x 4096 outputs."""
     n, steps, seed = 4096, 4096, 42
