@@ -93,7 +93,7 @@ static void init_small_primes(void)
 /* Trial division by 2 and the odd primes below 1024: returns 0 when n is
  * composite (or < 2), 1 when n is proven prime (n < 1024^2 with no factor
  * found), 2 when undecided. */
-static int small_factor_verdict(uint64_t n)
+static int small_factor_test(uint64_t n)
 {
     init_small_primes();
     if (n < 2)
@@ -143,7 +143,7 @@ static int miller_rabin(uint64_t n)
 
 int oracle_is_prime_u64(uint64_t n)
 {
-    int v = small_factor_verdict(n);
+    int v = small_factor_test(n);
     if (v != 2)
         return v;
     return miller_rabin(n);
@@ -159,10 +159,10 @@ int oracle_is_safe_multiplier(uint64_t a, int log2b)
         return 0;
     uint64_t p = a * ((uint64_t)1 << log2b) - 1;
     uint64_t q = (p - 1) / 2;
-    int vq = small_factor_verdict(q);
+    int vq = small_factor_test(q);
     if (vq == 0)
         return 0;
-    int vp = small_factor_verdict(p);
+    int vp = small_factor_test(p);
     if (vp == 0)
         return 0;
     return (vq == 1 || miller_rabin(q)) && (vp == 1 || miller_rabin(p));
