@@ -367,7 +367,10 @@ int rng_plan_launch(rng_plan_handle p, void *cuda_stream);
  * with the old one.  The tiles keep the items' order (no length ordering),
  * so that a serving loop can rebuild a plan every tick cheaply.  Allocates
  * device memory only when the list outgrows every earlier one (after waiting
- * for `cuda_stream`).  The host list is staged before the call returns.
+ * for `cuda_stream`).  The tiles are written to one of two pinned host lists
+ * owned by the plan, used in turn, and copied without the call waiting; a
+ * refill waits only if the copy out of its list (two refills earlier) has not
+ * finished.  `items` may be reused as soon as the call returns.
  * Errors: RNG_ERR_ARG (as rng_plan_create, or items on another device),
  * RNG_ERR_OOM, RNG_ERR_CUDA. */
 int rng_plan_refill(rng_plan_handle p, const rng_batch_item *items, size_t n_items,

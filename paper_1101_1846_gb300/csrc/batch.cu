@@ -297,14 +297,28 @@ struct Plan {
     unsigned long long *d_next = nullptr;
     int threads = kDefaultThreads;
     int grid = 0;
-    std::vector<Unit> host;          // refill staging
     std::vector<Claim> claims;       // refill overlap check
+    // refill staging: two pinned host lists used in turn, so that the copy
+    // to the device is a plain DMA and the call does not wait for it; a
+    // refill reuses a list after the copy out of it (two refills earlier)
+    // has finished (its event)
+    Unit *pinned[2] = {nullptr, nullptr};
+    uint64_t pinned_cap[2] = {0, 0};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    int turn = 0;
 };
 
 void free_plan(Plan *p)
 {
     if (!p)
         return;
+    for (int k = 0; k < 2; ++k) {
+        if (p->copied[k]) {
+            cudaEventSynchronize(p->copied[k]);
+            cudaEventDestroy(p->copied[k]);
+        }
+        cudaFreeHost(p->pinned[k]);
+    }
     cudaFree(p->d_units);
     cudaFree(p->d_next);
     delete p;
@@ -404,14 +418,30 @@ extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, s
     if (device != p->device)
         return set_error(RNG_ERR_ARG);
     const uint64_t n = fill_units(items, n_items, p->threads, nullptr, 0);
-    p->host.resize(n);
-    fill_units(items, n_items, p->threads, p->host.data(), n);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->device)
         cudaSetDevice(p->device);
-    if (n > p->cap_units) {
+    const int k = p->turn;
+    if (p->copied[k])  // the copy out of this list, two refills ago
+        st = cuda_status(cudaEventSynchronize(p->copied[k]));
+    else
+        st = cuda_status(cudaEventCreateWithFlags(&p->copied[k], cudaEventDisableTiming));
+    if (!st && n > p->pinned_cap[k]) {
+        cudaFreeHost(p->pinned[k]);
+        p->pinned[k] = nullptr;
+        p->pinned_cap[k] = 0;
+        const uint64_t cap = std::max<uint64_t>(n, 2 * p->pinned_cap[k ^ 1]);
+        if (cudaHostAlloc(reinterpret_cast<void **>(&p->pinned[k]), cap * sizeof(Unit),
+                          cudaHostAllocDefault) != cudaSuccess)
+            st = set_error(RNG_ERR_OOM);
+        else
+            p->pinned_cap[k] = cap;
+    }
+    if (!st)
+        fill_units(items, n_items, p->threads, p->pinned[k], n);
+    if (!st && n > p->cap_units) {
         // grow: wait for work that may still read the old list
         st = cuda_status(cudaStreamSynchronize(stream));
         Unit *grown = nullptr;
@@ -423,11 +453,15 @@ extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, s
             p->cap_units = n;
         }
     }
-    if (!st && n)  // pageable source: staged before the call returns
-        st = cuda_status(cudaMemcpyAsync(p->d_units, p->host.data(), n * sizeof(Unit),
+    if (!st && n)
+        st = cuda_status(cudaMemcpyAsync(p->d_units, p->pinned[k], n * sizeof(Unit),
                                          cudaMemcpyHostToDevice, stream));
     if (!st)
+        st = cuda_status(cudaEventRecord(p->copied[k], stream));
+    if (!st) {
         p->n_units = n;
+        p->turn ^= 1;
+    }
     if (prev >= 0 && prev != p->device)
         cudaSetDevice(prev);
     return st;
