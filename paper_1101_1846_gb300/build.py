@@ -37,7 +37,7 @@ def nvcc() -> str:
 
 
 def _deps() -> list[Path]:
-    return ([CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) +
+    return ([CSRC / s for s in SOURCES] + list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) +
             list(INCLUDE.glob("*.h")) + list(INCLUDE.glob("*.cuh")) + [Path(__file__)])
 
 

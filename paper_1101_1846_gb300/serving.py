@@ -58,11 +58,18 @@ class Server:
 
     def take_arrays(self) -> tuple[np.ndarray, np.ndarray]:
         """Completed requests as (ids, device completion times in ms)."""
-        got = self.take()
-        if not got:
-            return np.zeros(0, np.uint64), np.zeros(0)
-        ids, ms = zip(*got)
-        return np.array(ids, dtype=np.uint64), np.array(ms)
+        ids_all, ms_all = [], []
+        ids_view = np.ctypeslib.as_array(self._ids)
+        ms_view = np.ctypeslib.as_array(self._ms)
+        while True:
+            n = capi.lib().rng_server_take(self.h, self._ids, self._ms, len(self._ids))
+            ids_all.append(ids_view[:n].copy())
+            ms_all.append(ms_view[:n].copy())
+            if n < len(self._ids):
+                break
+        if len(ids_all) == 1:
+            return ids_all[0], ms_all[0]
+        return np.concatenate(ids_all), np.concatenate(ms_all)
 
     def release_many(self, ids: np.ndarray) -> None:
         ids = np.ascontiguousarray(ids, dtype=np.uint64)
