@@ -27,7 +27,10 @@ int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
 
 /* Sequence splitting of few-stream calls (rng_generate, rng_generate_reduce):
  * `log2_rows` is log2 of the fewest rows a segment may have for `kind`
- * (1..30); 0 turns splitting off for the kind.  Outputs never change. */
+ * (1..30); 0 turns splitting off for the kind.  A split generate call takes
+ * as many segments as bring its threads up to 2048 per SM (1024 for a
+ * consumer call), each a power-of-two number of rows no smaller than that.
+ * Outputs never change. */
 int gbrng_set_split(int kind, int log2_rows);
 int gbrng_get_split(int kind, int *log2_rows);
 
