@@ -84,3 +84,26 @@ def test_no_device_reports_nodev(lib):
         pytest.skip("a GPU is present")
     assert lib.rng_create(0, 16, 1) is None
     assert lib.rng_last_error() == capi.RNG_ERR_NODEV
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the Python layer raises; nothing falls back
+    to the host (run in a fresh interpreter so the loaded library of this
+    process is not involved)."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from pathlib import Path\n"
+        "from paper_1101_1846_gb300 import capi\n"
+        "capi.LIB_PATH = Path(%r)\n"
+        "from paper_1101_1846_gb300.generator import Generator\n"
+        "try:\n"
+        "    Generator(0, 16, 1)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised', 'missing' in str(e))\n"
+        "else:\n"
+        "    print('no error')\n"
+    ) % (str(ROOT), str(tmp_path / "absent" / "libgbrng.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.stdout.strip() == "raised True", r.stdout + r.stderr[-2000:]
