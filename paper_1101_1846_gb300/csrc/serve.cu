@@ -18,6 +18,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "gbrng.cuh"
 
 namespace gbrng {
@@ -27,58 +28,6 @@ constexpr uint64_t kGranule = 256;  // arena alignment, bytes
 constexpr int kMaxInflight = 2;     // ticks in flight per lane
 constexpr int kLanes = 2;           // client c belongs to lane c % kLanes
 constexpr int kServeThreads = 512;
-
-// First-fit allocator over [0, size) bytes in kGranule units.
-class Arena {
-public:
-    explicit Arena(uint64_t size) : size_(size / kGranule * kGranule)
-    {
-        if (size_)
-            free_[0] = size_;
-    }
-    bool alloc(uint64_t bytes, uint64_t *off)
-    {
-        bytes = (bytes + kGranule - 1) / kGranule * kGranule;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                uint64_t rest = it->second - bytes;
-                uint64_t at = it->first + bytes;
-                free_.erase(it);
-                if (rest)
-                    free_[at] = rest;
-                used_ += bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(uint64_t off, uint64_t bytes)
-    {
-        bytes = (bytes + kGranule - 1) / kGranule * kGranule;
-        used_ -= bytes;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + bytes == next->first) {
-            bytes += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += bytes;
-                return;
-            }
-        }
-        free_[off] = bytes;
-    }
-    uint64_t used() const { return used_; }
-    uint64_t size() const { return size_; }
-
-private:
-    uint64_t size_;
-    uint64_t used_ = 0;
-    std::map<uint64_t, uint64_t> free_;
-};
 
 struct Req {
     uint32_t client = 0;
@@ -380,7 +329,7 @@ extern "C" rng_server_handle rng_server_create(int kind, uint32_t n_clients,
     if (cudaMalloc(&S->arena_base, arena) != cudaSuccess)
         st = set_error(RNG_ERR_OOM);
     if (!st)
-        S->arena = new (std::nothrow) Arena(arena);
+        S->arena = new (std::nothrow) Arena(arena, kGranule);
     if (!st && !S->arena)
         st = set_error(RNG_ERR_OOM);
     for (int ln = 0; ln < kLanes && !st; ++ln)
