@@ -13,7 +13,6 @@
 // disjoint stream ranges of one generator, all in the same launch.
 #include <algorithm>
 #include <deque>
-#include <map>
 #include <new>
 #include <unordered_map>
 #include <vector>
