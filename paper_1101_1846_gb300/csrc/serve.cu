@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "arena.h"
+#include "pieces.h"
 #include "gbrng.cuh"
 
 namespace gbrng {
@@ -86,26 +87,6 @@ struct DeviceScope {
             cudaSetDevice(prev);
     }
 };
-
-// Items of one piece: m samples of `h` from sample c on, written to out.
-void piece_items(rng_handle h, uint64_t n, uint64_t c, uint64_t m, uint32_t *out, int fmt,
-                 std::vector<rng_batch_item> &items)
-{
-    const uint64_t r = c % n, q = m / n, rem = m % n;
-    auto columns = [&](uint64_t c0, uint64_t c1, uint64_t rows) {
-        if (rows == 0 || c0 >= c1)
-            return;
-        const uint64_t a1 = std::min(c1, n - r);  // columns [c0, a1): streams r + col
-        if (c0 < a1)
-            items.push_back(rng_batch_item{h, rows, out + c0, fmt, r + c0, r + a1, n});
-        const uint64_t b0 = std::max(c0, n - r);  // columns [b0, c1): streams col - (n - r)
-        if (b0 < c1)
-            items.push_back(
-                rng_batch_item{h, rows, out + b0, fmt, b0 - (n - r), c1 - (n - r), n});
-    };
-    columns(0, rem, q + 1);
-    columns(rem, n, q);
-}
 
 int retire(Server *S)
 {
