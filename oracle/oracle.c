@@ -8,7 +8,8 @@
  * and bench.py's CPU baseline / reference arm may load it.  It shares no code
  * with the CUDA library.
  *
- * Parity status of each part (what pins it is in tests/test_oracle_pins.py):
+ * Parity status of each part (what pins it is in tests/test_oracle_pins.py and
+ * tests/test_oracle_seeding.py):
  *   primality, multiplier search ... pinned (392 count of Sec. "Methods /
  *                                    multiply-with-carry"; brute force)
  *   MWC step ....................... pinned (Lehmer closed form; periods)
@@ -19,9 +20,12 @@
  *   LCG step ....................... pinned (Eq. 7 constants; period 2^32)
  *   KISS combination ............... pinned (sum of independently stepped parts)
  *   FP32 uniform ................... pinned (exactness, range)
- *   splitmix64 seeding ............. increment pinned (golden ratio); the
- *                                    finaliser constants are parity unpinned
- *                                    beyond a published test value
+ *   splitmix64 ..................... pinned (increment = golden ratio;
+ *                                    published outputs from three states)
+ *   seeding, every kind ............ pinned (the draw-to-state mapping
+ *                                    restated with Python integers; each
+ *                                    redraw branch reached by a seed found by
+ *                                    inverting the finaliser)
  *   consumers (sums, disc count) ... pinned (closed-form sums of synthetic
  *                                    sequences; lattice count of the quarter
  *                                    disc by integer square roots)

@@ -2,6 +2,8 @@
 that the pins in test_oracle_pins.py catch each one."""
 from __future__ import annotations
 
+from functools import partial
+
 import numpy as np
 import pytest
 
@@ -10,6 +12,7 @@ import test_oracle_battery as bat
 import test_oracle_consumers_jump as cj
 import test_oracle_paper_variants as pv
 import test_oracle_pins as pins
+import test_oracle_seeding as sd
 
 SRC = (oracle.HERE / "oracle.c").read_text()
 
@@ -96,6 +99,39 @@ MUTANTS = [
      "b[i] = u[(blk * 512 + i) * n_streams + s] >> 7;", bat.check_birthday_repeats),
     ("birthday without the sample cap", "s < n_streams && samples < ORACLE_BAT_BIRTHDAY_MAX;",
      "s < n_streams;", bat.check_birthday_cap_and_order),
+    ("splitmix64 shift 27->26", "r = (r ^ (r >> 27))", "r = (r ^ (r >> 26))",
+     sd.check_splitmix64_published_vectors),
+    ("stream seed is seed xor s", "uint64_t z = seed + s;", "uint64_t z = seed ^ s;",
+     partial(sd.check_seeding_mapping, oracle.XOR128)),
+    ("xor128 seed lo/hi swapped", "st[0] = lo32(r0);\n            st[1] = hi32(r0);",
+     "st[0] = hi32(r0);\n            st[1] = lo32(r0);", partial(sd.check_seeding_mapping, oracle.XOR128)),
+    ("MWC seed carry not reduced", "*c = hi32(r) % a;", "*c = hi32(r);",
+     partial(sd.check_seeding_redraws, oracle.MWC)),
+    ("MWC seed keeps (0, 0)", "int zero = (*x == 0 && *c == 0);", "int zero = 0;",
+     partial(sd.check_seeding_redraws, oracle.MWC)),
+    ("MWC seed keeps the top fixed point", "int top = (*x == 0xFFFFFFFFu && *c == a - 1);",
+     "int top = 0;", partial(sd.check_seeding_redraws, oracle.MWC)),
+    ("KISS seed y and z swapped",
+     "st[2] = lo32(r);\n        st[3] = hi32(r);\n        while (st[2] == 0)\n            st[2] = lo32(oracle_splitmix64(&z));\n    }\n}",
+     "st[2] = hi32(r);\n        st[3] = lo32(r);\n        while (st[2] == 0)\n            st[2] = lo32(oracle_splitmix64(&z));\n    }\n}",
+     partial(sd.check_seeding_mapping, oracle.KISS)),
+    ("KISS seed keeps y = 0",
+     "        while (st[2] == 0)\n            st[2] = lo32(oracle_splitmix64(&z));\n    }\n}",
+     "    }\n}", partial(sd.check_seeding_redraws, oracle.KISS)),
+    ("KISS_XOR seed keeps y = 0",
+     "        while (st[2] == 0)\n            st[2] = lo32(oracle_splitmix64(&z));\n        return;",
+     "        return;", partial(sd.check_seeding_redraws, oracle.KISS_XOR)),
+    ("MWC16X2 seed halves swapped",
+     "zw[0] = x1 | (c1 << 16);\n            zw[1] = x2 | (c2 << 16);",
+     "zw[0] = x2 | (c2 << 16);\n            zw[1] = x1 | (c1 << 16);",
+     partial(sd.check_seeding_mapping, oracle.MWC16X2)),
+    ("MWC16X2 seed part two from bits 31-46", "(uint32_t)((r >> 32) & 0xFFFFu)",
+     "(uint32_t)((r >> 31) & 0xFFFFu)", partial(sd.check_seeding_mapping, oracle.MWC16X2)),
+    ("MWC16X2 seed carry one not reduced", "(uint32_t)((r >> 16) & 0xFFFFu) % a1",
+     "(uint32_t)((r >> 16) & 0xFFFFu)", partial(sd.check_seeding_mapping, oracle.MWC16X2)),
+    ("XORSHIFT8 seed lo/hi swapped", "st[2 * i] = lo32(r);\n                st[2 * i + 1] = hi32(r);",
+     "st[2 * i] = hi32(r);\n                st[2 * i + 1] = lo32(r);",
+     partial(sd.check_seeding_mapping, oracle.XORSHIFT8)),
 ]
 
 
