@@ -281,8 +281,12 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    # weak scaling: every rank owns its own n streams, seeds shifted by rank*n
-    gens = {k: Generator(k, n, replicas.rank_seed(args.seed, rank, n)) for k in KINDS}
+    # weak scaling: rank r owns global streams r*n .. (r+1)*n - 1 of one
+    # generator per kind (replicas.shard_spec)
+    gens = {}
+    for k in KINDS:
+        s_begin, seed_k = replicas.shard_spec(k, rank, world, n, args.seed)
+        gens[k] = Generator(k, n, seed_k, s_begin=s_begin)
     out = torch.empty((steps, n), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     pairs = [(k, f) for k in KINDS for f in FMTS]

@@ -124,6 +124,18 @@ enum rng_status {
  * Sec. "Parallelizing RNGs"). */
 rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed);
 
+/* Creates a generator that holds streams s_begin .. s_begin + n_streams - 1
+ * of the generator rng_create(kind, s_begin + n_streams, seed) would make:
+ * its stream s gets global stream s_begin + s's multiplier (or pair) and
+ * its seed, splitmix64 started at seed + s_begin + s.  Every output and
+ * state is then equal to that stream of the one large generator, so a
+ * stream range can live on its own device (one range per GPU) and no call
+ * ever exchanges data between ranges.  RNG_ERR_ARG when s_begin + n_streams
+ * exceeds the kind's maximum stream count; other errors as rng_create.
+ * Paper: parametrisation, each stream its own multiplier and seeds
+ * (Sec. "Parallelizing RNGs"). */
+rng_handle rng_create_range(int kind, uint64_t s_begin, uint64_t n_streams, uint64_t seed);
+
 /* Releases the handle and its device memory (waits for its stream first).
  * NULL is ignored. */
 void rng_destroy(rng_handle h);
@@ -511,6 +523,9 @@ void rng_server_destroy(rng_server_handle s);
  * at most one when c % 4 != 0); more returns RNG_ERR_ARG and launches nothing.  No cudaMalloc, cudaFree or other allocating routine is
  * called.  The first call on a device looks up the device address of that
  * array (once per device), so make the first call before any stream capture.
+ * That address is kept until the process exits, like the library's other
+ * per-device tables: cudaDeviceReset is not supported while the library is
+ * in use.
  * Asynchronous on `cuda_stream`: the work list is copied from library host
  * memory before the call returns.  Every call shares the one array, which
  * keeps the last call's contents; calls whose kernels overlap on the GPU

@@ -51,6 +51,8 @@ class rng_battery_counts(ctypes.Structure):
 # name -> (restype, argtypes); every symbol declared in include/*.h
 SIGNATURES = {
     "rng_create": (ctypes.c_void_p, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]),
+    "rng_create_range": (ctypes.c_void_p, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_uint64]),
     "rng_destroy": (None, [ctypes.c_void_p]),
     "rng_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "rng_n_streams": (ctypes.c_uint64, [ctypes.c_void_p]),

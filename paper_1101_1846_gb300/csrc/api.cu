@@ -97,9 +97,16 @@ int cuda_status(cudaError_t e)
 
 using namespace gbrng;
 
-extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
+namespace gbrng {
+namespace {
+
+// Streams s_begin .. s_begin + n_streams of the generator (kind, seed): the
+// handle's stream s is global stream s_begin + s, with that stream's
+// multiplier and splitmix64 started at seed + s_begin + s.
+rng_handle create_range(int kind, uint64_t s_begin, uint64_t n_streams, uint64_t seed)
 {
-    if (!valid_kind(kind) || n_streams == 0 || n_streams > max_streams(kind)) {
+    if (!valid_kind(kind) || n_streams == 0 || s_begin > max_streams(kind) ||
+        n_streams > max_streams(kind) - s_begin) {
         set_error(RNG_ERR_ARG);
         return nullptr;
     }
@@ -116,7 +123,7 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     g->kind = kind;
     g->device = dev;
     g->n = n_streams;
-    g->seed = seed;
+    g->seed = seed + s_begin;
     g->words = words_of(kind);
     int st = RNG_OK;
     if (cudaMalloc(&g->d_state, (size_t)g->words * n_streams * 4) != cudaSuccess) {
@@ -124,12 +131,14 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
     } else if (has_mult(kind)) {
         // one multiplier per stream, or one packed pair for the base-2^16 kinds
         const uint32_t *table = nullptr;
-        st = kind == RNG_MWC16X2 || kind == RNG_KISS_XOR ? mwc16_pair_table(n_streams, &table)
-                                                         : multiplier_table(n_streams, &table);
+        const uint64_t need = s_begin + n_streams;
+        st = kind == RNG_MWC16X2 || kind == RNG_KISS_XOR ? mwc16_pair_table(need, &table)
+                                                         : multiplier_table(need, &table);
         if (!st && cudaMalloc(&g->d_a, n_streams * 4) != cudaSuccess)
             st = set_error(RNG_ERR_OOM);
         if (!st)
-            st = cuda_status(cudaMemcpy(g->d_a, table, n_streams * 4, cudaMemcpyDeviceToDevice));
+            st = cuda_status(cudaMemcpy(g->d_a, table + s_begin, n_streams * 4,
+                                        cudaMemcpyDeviceToDevice));
     }
     // buffers of split calls (few streams only): the final-state stash, the
     // arrival counters (zero) and the MWC jump multipliers
@@ -155,6 +164,20 @@ extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
         return nullptr;
     }
     return reinterpret_cast<rng_handle>(g);
+}
+
+}  // namespace
+}  // namespace gbrng
+
+extern "C" rng_handle rng_create(int kind, uint64_t n_streams, uint64_t seed)
+{
+    return create_range(kind, 0, n_streams, seed);
+}
+
+extern "C" rng_handle rng_create_range(int kind, uint64_t s_begin, uint64_t n_streams,
+                                       uint64_t seed)
+{
+    return create_range(kind, s_begin, n_streams, seed);
 }
 
 extern "C" void rng_destroy(rng_handle h)

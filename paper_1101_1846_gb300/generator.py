@@ -25,15 +25,20 @@ class Generator:
     row j holds output j of every stream (the stream-interleaved layout).
     uint32 outputs are returned in an int32 tensor (same bits)."""
 
-    def __init__(self, kind: int | str, n_streams: int, seed: int):
+    def __init__(self, kind: int | str, n_streams: int, seed: int, s_begin: int = 0):
         kind = capi.KINDS.get(kind, kind) if isinstance(kind, str) else kind
-        h = capi.lib().rng_create(int(kind), int(n_streams), int(seed) & (2**64 - 1))
+        if s_begin:  # streams s_begin .. s_begin + n_streams - 1 of one generator
+            h = capi.lib().rng_create_range(int(kind), int(s_begin), int(n_streams),
+                                            int(seed) & (2**64 - 1))
+        else:
+            h = capi.lib().rng_create(int(kind), int(n_streams), int(seed) & (2**64 - 1))
         if not h:
             raise capi.RngError(capi.lib().rng_last_error(), "rng_create")
         self.h = h
         self.kind = int(kind)
         self.n_streams = int(n_streams)
         self.seed = int(seed)
+        self.s_begin = int(s_begin)
         self.words = capi.lib().rng_state_words(h)
         self.device = torch.cuda.current_device()
 

@@ -1,14 +1,17 @@
 """Host logic of runs on several GPUs.  The streams are independent (the
 paper parametrises every thread's generator: Sec. "Parallelizing RNGs"), so
-the path shards with no collective on the data path: each rank owns its own
-streams, and the ranks only agree on timing.
+the path shards with no collective on the data path: each rank owns a
+contiguous range of one global generator's streams, and the ranks only agree
+on timing.
 
-- rank_seed: rank r's generator of n streams is seeded with seed + r * n, so
-  its stream s starts splitmix64 at seed + r * n + s — the same point as
-  stream r * n + s of one generator of world * n streams seeded with seed.
-  Streams of different ranks therefore never share a seeding point, and for
-  the kinds without per-stream multipliers (xor128, XORSHIFT8) rank r
-  produces exactly that generator's streams r * n .. (r + 1) * n - 1.
+- shard_spec: rank r of `world` ranks with n streams each holds global
+  streams r * n .. (r + 1) * n - 1 of the generator (kind, seed): a handle
+  made by rng_create_range(kind, r * n, n, seed), with those streams'
+  multipliers and seeds.  When world * n streams exceed the kind's
+  multiplier table (MWC32 and KISS at 2^22 streams per rank), the rank
+  keeps the table's first n multipliers and shifts its seed by r * n
+  instead (rank_seed): its streams then start splitmix64 at the same points
+  as the global streams, on the same multipliers as rank 0.
 - max_over_ranks: the slowest rank's time, which the whole job's rate uses.
 - job_rate: samples of all ranks over that time (weak scaling).
 """
@@ -17,9 +20,26 @@ from __future__ import annotations
 import torch
 import torch.distributed as dist
 
+from . import capi
+
+# largest stream count of each kind (include/rng.h)
+MAX_STREAMS = {0: capi.RNG_MAX_STREAMS_MWC, 1: capi.RNG_MAX_STREAMS_XOR,
+               2: capi.RNG_MAX_STREAMS_MWC, 3: capi.RNG_MAX_STREAMS_MWC16,
+               4: capi.RNG_MAX_STREAMS_XS8, 5: capi.RNG_MAX_STREAMS_MWC16}
+
 
 def rank_seed(seed: int, rank: int, n_streams: int) -> int:
     return (seed + rank * n_streams) % (1 << 64)
+
+
+def shard_spec(kind: int, rank: int, world: int, n_streams: int, seed: int) -> tuple[int, int]:
+    """(s_begin, seed) to create rank `rank`'s handle with: rng_create_range
+    (kind, s_begin, n_streams, seed) holds global streams s_begin ..
+    s_begin + n_streams - 1.  s_begin is 0, with the seed shifted, when the
+    global generator would have more streams than the kind allows."""
+    if world * n_streams <= MAX_STREAMS[kind]:
+        return rank * n_streams, seed % (1 << 64)
+    return 0, rank_seed(seed, rank, n_streams)
 
 
 def max_over_ranks(value: float, device: torch.device | str = "cpu") -> float:

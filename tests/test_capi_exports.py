@@ -59,6 +59,10 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.rng_last_error() == capi.RNG_ERR_ARG
     assert lib.rng_create(2, capi.RNG_MAX_STREAMS_MWC + 1, 1) is None
     assert lib.rng_last_error() == capi.RNG_ERR_ARG
+    assert lib.rng_create_range(2, capi.RNG_MAX_STREAMS_MWC, 1, 1) is None
+    assert lib.rng_last_error() == capi.RNG_ERR_ARG
+    assert lib.rng_create_range(1, 2**64 - 1, 2, 1) is None  # s_begin + n wraps
+    assert lib.rng_last_error() == capi.RNG_ERR_ARG
     assert lib.rng_generate(None, 4, None, 0) == capi.RNG_ERR_ARG
     assert lib.rng_get_state(None, None, 0) == capi.RNG_ERR_ARG
     assert lib.rng_plan_create(None, 0, 0, 0) is None

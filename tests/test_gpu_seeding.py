@@ -67,3 +67,34 @@ def test_device_seeding_takes_every_redraw_branch(kind):
                 out = g.generate(9).cpu().view(torch.int32).numpy().view(np.uint32)
             ref, _ = oracle.generate(kind, a_tab, exp, 9, oracle.U32)
             assert np.array_equal(out, ref), (kind, s, idx)
+
+
+@pytest.mark.parametrize("kind", range(6))
+def test_range_handle_is_the_slice_of_the_whole_generator(kind):
+    """rng_create_range(kind, s_begin, n, seed) gives the streams s_begin ..
+    s_begin + n - 1 of rng_create(kind, s_begin + n, seed): the same
+    multipliers, states and outputs, over two carried calls; and the oracle
+    agrees."""
+    n, s_begin, seed, steps = 300, 1000, 4242, 17
+    with Generator(kind, s_begin + n, seed) as whole, \
+            Generator(kind, n, seed, s_begin=s_begin) as part:
+        for _ in range(2):
+            w = whole.generate(steps).cpu().view(torch.int32).numpy().view(np.uint32)
+            p = part.generate(steps).cpu().view(torch.int32).numpy().view(np.uint32)
+            assert np.array_equal(p, w[:, s_begin:])
+        ws = whole.get_state().numpy()
+        assert np.array_equal(part.get_state().numpy(), ws[:, s_begin:])
+    table = oracle.multipliers_for(kind, s_begin + n)
+    a = None if table is None else table[s_begin:]
+    st = oracle.seed_streams(kind, a, seed + s_begin, np.arange(n))
+    exp, _ = oracle.generate(kind, a, st, 2 * steps, oracle.U32)
+    assert np.array_equal(p, exp[steps:])
+
+
+def test_range_handle_rejects_ranges_beyond_the_table():
+    L = capi.lib()
+    assert L.rng_create_range(0, capi.RNG_MAX_STREAMS_MWC - 10, 11, 1) is None
+    assert L.rng_last_error() == capi.RNG_ERR_ARG
+    h = L.rng_create_range(0, capi.RNG_MAX_STREAMS_MWC - 10, 10, 1)
+    assert h
+    L.rng_destroy(h)

@@ -1,6 +1,6 @@
-"""The multi-GPU host logic with two gloo ranks on the CPU (no GPU): rank
-seeding covers a single generator's streams without overlap, and the job's
-time is the slowest rank's."""
+"""The multi-GPU host logic with two gloo ranks on the CPU (no GPU): each
+rank's stream range is its slice of one generator's streams, multipliers
+included, and the job's time is the slowest rank's."""
 from __future__ import annotations
 
 import os
@@ -44,18 +44,38 @@ def test_two_gloo_ranks_agree_on_the_slowest_time():
     assert res[0][2] == res[1][2] == 2 * 5000 / 2.0
 
 
-def test_rank_streams_are_the_global_generators_streams():
-    """For xor128 (no per-stream multipliers) rank r's n streams are streams
-    r*n .. (r+1)*n - 1 of one generator of world*n streams (oracle, CPU)."""
+def _rank_outputs(kind, rank, world, n, seed, steps):
+    """What rng_create_range(kind, s_begin, n, seed') computes, for the
+    (s_begin, seed') of shard_spec: the handle's stream s takes multiplier
+    s_begin + s of the table and starts splitmix64 at seed' + s_begin + s
+    (oracle, CPU)."""
+    import oracle
+    s_begin, seed_r = replicas.shard_spec(kind, rank, world, n, seed)
+    table = oracle.multipliers_for(kind, s_begin + n)
+    a = None if table is None else table[s_begin:s_begin + n]
+    st = oracle.seed_streams(kind, a, (seed_r + s_begin) % (1 << 64), np.arange(n))
+    return oracle.generate(kind, a, st, steps, oracle.U32)[0]
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 5])
+def test_rank_streams_are_the_global_generators_streams(kind):
+    """Rank r's n streams are streams r*n .. (r+1)*n - 1 of one generator of
+    world*n streams, multipliers included (oracle, CPU)."""
     import oracle
     n, world, seed = 64, 3, 7
-    whole = oracle.seed_streams(oracle.XOR128, None, seed, np.arange(world * n))
-    ref, _ = oracle.generate(oracle.XOR128, None, whole, 16, oracle.U32)
+    table = oracle.multipliers_for(kind, world * n)
+    whole = oracle.seed_streams(kind, table, seed, np.arange(world * n))
+    ref, _ = oracle.generate(kind, table, whole, 16, oracle.U32)
     for r in range(world):
-        st = oracle.seed_streams(oracle.XOR128, None, replicas.rank_seed(seed, r, n),
-                                 np.arange(n))
-        out, _ = oracle.generate(oracle.XOR128, None, st, 16, oracle.U32)
-        assert np.array_equal(out, ref[:, r * n:(r + 1) * n])
+        out = _rank_outputs(kind, r, world, n, seed, 16)
+        assert np.array_equal(out, ref[:, r * n:(r + 1) * n]), (kind, r)
+
+
+def test_shard_spec_falls_back_to_shifted_seeds_beyond_the_table():
+    n = replicas.MAX_STREAMS[0]
+    assert replicas.shard_spec(0, 0, 1, n, 5) == (0, 5)
+    assert replicas.shard_spec(0, 1, 2, n, 5) == (0, 5 + n)   # 2n > 2^22 multipliers
+    assert replicas.shard_spec(1, 1, 2, n, 5) == (n, 5)       # xor128 has no table
 
 
 def test_no_group_means_own_value():

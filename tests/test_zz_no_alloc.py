@@ -75,6 +75,27 @@ def test_noalloc_batch_equals_batch_on_two_calls():
             assert torch.equal(ga[k].get_state(), gb[k].get_state()), (call, k)
 
 
+def test_noalloc_batch_allocates_no_device_memory():
+    """After a first call (which loads the kernel and looks up the scratch
+    address), further calls leave the device's free memory and torch's
+    allocator exactly as they were."""
+    ins = _instances(count=24, seed=99)
+    gens, outs = _twin(ins)
+    arr = _items(ins, gens, outs)
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = capi.lib()
+    assert L.rng_generate_batch_noalloc(arr, len(ins), sp) == capi.RNG_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert L.rng_generate_batch_noalloc(arr, len(ins), sp) == capi.RNG_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_batch_rejects_work_beyond_its_capacity():
     g = Generator(capi.RNG_XOR128, 1 << 25, 9)  # 65536 tiles of 512 streams
     out = torch.zeros(1 << 25, dtype=torch.int32, device="cuda")
