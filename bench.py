@@ -34,6 +34,7 @@ KNAME = {0: "mwc", 1: "xor128", 2: "kiss"}
 FNAME = {0: "u32", 1: "f32"}
 STATE_WORDS = {0: 2, 1: 4, 2: 4}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def parse():
@@ -45,7 +46,7 @@ def parse():
     p.add_argument("--n-streams", type=int, default=1 << 22)
     p.add_argument("--n-per-stream", type=int, default=1024)
     p.add_argument("--seed", type=int, default=42)
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (batched, serving, other configs)")
@@ -125,6 +126,18 @@ def recorded_traffic(kernel: str, workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def recorded_pipes(kernel: str):
+    """Per-pipe utilisation (% of peak) of a generate kernel from the
+    committed ncu record, if it was taken on the current kernel source."""
+    f = ROOT / "profiles" / "int_pipes.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("kernels", {}).get(kernel)
+
+
 # ----------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -186,6 +199,109 @@ def gpu_selector(torch) -> str | None:
     return None
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; on Arm the
+    implementer and part codes when no name is given)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        info = Path("/proc/cpuinfo").read_text()
+    except OSError:
+        return "unknown"
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            fields.setdefault(k, v)
+    if "model name" in fields:
+        return fields["model name"]
+    return f"implementer {fields.get('CPU implementer', '?')} part {fields.get('CPU part', '?')}"
+
+
+def gpu_pci_dir(torch, dev: int) -> Path | None:
+    p = torch.cuda.get_device_properties(dev)
+    d = Path(f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:"
+             f"{p.pci_device_id:02x}.0")
+    return d if d.exists() else None
+
+
+def _cpulist(text: str) -> set[int]:
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def gpu_local_cpus(torch, dev: int) -> tuple[int | None, set[int]]:
+    """The GPU's NUMA node and the CPUs near it (from sysfs), intersected
+    with the CPUs this process may run on."""
+    d = gpu_pci_dir(torch, dev)
+    node, cpus = None, set()
+    if d is not None:
+        try:
+            node = int((d / "numa_node").read_text())
+            cpus = _cpulist((d / "local_cpulist").read_text())
+        except (OSError, ValueError):
+            pass
+    if node is not None and node >= 0 and not cpus:
+        try:
+            cpus = _cpulist(Path(f"/sys/devices/system/node/node{node}/cpulist").read_text())
+        except OSError:
+            pass
+    return node, cpus & os.sched_getaffinity(0)
+
+
+def numa_pages(addr: int) -> dict[str, int]:
+    """Pages per NUMA node of the mapping that holds `addr`
+    (/proc/self/numa_maps)."""
+    best, fields = -1, ""
+    try:
+        for line in Path("/proc/self/numa_maps").read_text().splitlines():
+            start, rest = line.split(" ", 1)
+            a = int(start, 16)
+            if best < a <= addr:
+                best, fields = a, rest
+    except (OSError, ValueError):
+        return {}
+    out = {}
+    for tok in fields.split():
+        if tok.startswith("N") and "=" in tok:
+            k, v = tok.split("=", 1)
+            if k[1:].isdigit():
+                out[k] = int(v)
+    return out
+
+
+def pinned_near_gpu(torch, shape, dev: int):
+    """A pinned host tensor allocated while this thread runs on the CPUs
+    near the GPU, so that first touch places its pages on the GPU's own
+    node; returns the tensor and where its pages are."""
+    node, cpus = gpu_local_cpus(torch, dev)
+    old = os.sched_getaffinity(0)
+    placed = False
+    try:
+        if cpus and cpus != old:
+            os.sched_setaffinity(0, cpus)
+            placed = True
+        # cudaHostAlloc pins (and so first-touches) every page in this thread
+        host = torch.empty(shape, dtype=torch.int32, pin_memory=True)
+    finally:
+        if placed:
+            os.sched_setaffinity(0, old)
+    info = {"gpu_numa_node": node, "near_cpus": len(cpus), "allocated_on_near_cpus": placed,
+            "buffer_pages_by_node": numa_pages(host.data_ptr())}
+    return host, info
+
+
 # ---------------------------------------------------------------- oracle
 def _oracle_worker(args):
     kind, fmt, m, steps, seed, a = args
@@ -224,6 +340,27 @@ def cpu_baseline(steps_per_stream: int, streams_per_job: int = 1 << 13, seed: in
                       f"x {steps_per_stream} outputs ({samples / 1e6:.0f} M samples, "
                       f"{cpu_s:.1f} CPU-s, {wall:.1f} s wall)",
             "samples": samples, "wall_s": wall, "np_version": np.__version__}
+
+
+def cpu_single_thread(samples_per_pair: int = 1 << 26, seed: int = 42):
+    """The oracle on one host core: a slice of samples_per_pair samples
+    (2^16 streams x 1024 outputs) of every (kind, format) pair, as the
+    paper's single-thread CPU rows (Table IV).  Runs in a spawned process so
+    that the parent's CUDA context is not shared."""
+    steps = 1024
+    m = samples_per_pair // steps
+    ctx = mp.get_context("spawn")
+    import oracle
+    oracle.build()
+    a = oracle.multipliers(m, 32)
+    with ctx.Pool(1) as pool:
+        res = pool.map(_oracle_worker, [(k, f, m, steps, seed, a) for k in KINDS for f in FMTS],
+                       chunksize=1)
+    pairs = {f"{KNAME[k]}_{FNAME[f]}": r[0] / r[1] / 1e9
+             for (k, f), r in zip([(k, f) for k in KINDS for f in FMTS], res)}
+    return {"unit": UNIT, "cores": 1, "sample": f"{m} streams x {steps} outputs per "
+            "(kind, fmt) pair", "gsamples_s": pairs,
+            "paper_q6600_single_thread_gsamples_s": {"mwc": 0.3, "xorshift": 0.1, "kiss": 0.2}}
 
 
 # ------------------------------------------------------------- reference arm
@@ -341,7 +478,18 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": recorded_traffic(dom, workload),
                 "kernel": dom, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, "
                 "copy read+write)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": alg_bytes(dk, n, steps)}
+                "algorithmic_bytes_per_launch": alg_bytes(dk, n, steps),
+                "nominal_gbs": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    # the integer pipes of every writeback kernel, against the probed peaks
+    probes = run_int_probes((clock_info or {}).get("sm_mhz") or 2070.0, device_sms())
+    for (k, f) in pairs:
+        pk = per_kernel[f"{KNAME[k]}_{FNAME[f]}"]
+        pk["int"] = int_roofline(k, f, pk["gsamples_s"] * 1e9, probes)
+        rec = recorded_pipes(f"{KNAME[k]}_{FNAME[f]}")
+        if rec:
+            pk["int"]["ncu_pipes_pct"] = rec
+    roofline["int"] = per_kernel[dom]["int"]
+    roofline["int_probes"] = probes
 
     # write-only bandwidth probe over the same buffer (context for the roofline)
     nbytes = out.numel() * 4
@@ -361,7 +509,22 @@ def run_ours(args):
     if args.e2e_steps > 0:
         del out
         torch.cuda.empty_cache()
-        host = torch.empty((steps, n), dtype=torch.int32, pin_memory=True)
+        host, placement = pinned_near_gpu(torch, (steps, n), local)
+        # the link itself: a plain device-to-host copy of (up to) 1 GiB into
+        # the same pinned buffer, best of three
+        m = min(1 << 28, host.numel())
+        src = torch.empty(m, dtype=torch.int32, device="cuda")
+        dst = host.view(-1)[:m]
+        link = []
+        for _ in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            link.append(a.elapsed_time(b))
+        link_gbs = 4 * m / (min(link[1:]) * 1e-3) / 1e9
+        del src
         for k, f in pairs[:1]:
             gens[k].generate_host(steps, f, out=host)  # warm-up (staging buffers)
         torch.cuda.synchronize()
@@ -377,7 +540,10 @@ def run_ours(args):
         e2e = {"value": e2e_samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": len(pairs) * n * steps * 4,
                "steps": args.e2e_steps,
-               "api": "rng_generate_host into pinned host memory"}
+               "api": "rng_generate_host into pinned host memory",
+               "d2h_gbs": len(pairs) * n * steps * 4 * args.e2e_steps / dt / 1e9,
+               "plain_copy_d2h_gbs": link_gbs, "host_buffer": placement}
+        e2e["of_plain_copy"] = e2e["d2h_gbs"] / link_gbs
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -389,6 +555,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(steps, 1 << 15)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["cpu_model"] = cpu_model()
+        cpu["single_thread"] = cpu_single_thread()
 
     if rank == 0:
         line = {
@@ -431,7 +599,7 @@ def run_batched(args):
     every wave bit for bit against plain calls."""
     import torch
 
-    from paper_1101_1846_gb300 import autotune, capi, scheduler, workloads
+    from paper_1101_1846_gb300 import autotune, capi, laned, scheduler, workloads
     from paper_1101_1846_gb300.generator import BatchItem, Generator, Plan
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -439,26 +607,20 @@ def run_batched(args):
     inst = workloads.batched_instances(args.instances, 1234)
     budget = int(args.wave_gib * (1 << 30))
     lanes = max(1, args.lanes)
-    laned = scheduler.laned_waves([i.n_streams for i in inst], [i.n_per_stream for i in inst],
-                                  budget, args.chunk_rows, lanes)
-    waves = [w for _, w in laned]
+    laned_pairs = scheduler.laned_waves([i.n_streams for i in inst],
+                                        [i.n_per_stream for i in inst], budget,
+                                        args.chunk_rows, lanes)
+    waves = [w for _, w in laned_pairs]
     main = torch.cuda.current_stream()
     # A lane's waves continue the same instances, so they run in order on the
     # lane's stream and reuse the lane's buffer; lanes share no instance and
     # overlap.  The check pass below needs two buffers.
-    streams = [torch.cuda.Stream() for _ in range(lanes)]
     R = max(2, lanes)
     longest = max(4 * i.n_streams * i.n_per_stream for i in inst)  # plain calls write whole
     cap = max(budget, longest) // 4 + 4 * max(len(w) for w in waves)
     bufs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(R)]
-
-    def carve(buf, wave):
-        outs, off = [], 0
-        for p in wave:
-            m = inst[p.inst].n_streams * p.rows
-            outs.append(buf[off:off + m])
-            off += (m + 3) // 4 * 4  # 16-byte aligned starts
-        return outs
+    n_streams = [i.n_streams for i in inst]
+    fmts = [i.fmt for i in inst]
 
     def make_gens():
         return [Generator(i.kind, i.n_streams, i.seed) for i in inst]
@@ -473,41 +635,24 @@ def run_batched(args):
     shape, tune_ms = (0, 0), None
     if args.tune:
         tg = make_gens()
-        shape, tune_ms = autotune.tune_plan(items_for(tg, waves[0], carve(bufs[0], waves[0])))
+        shape, tune_ms = autotune.tune_plan(items_for(tg, waves[0],
+                                                      laned.carve(bufs[0], waves[0], n_streams)))
         for g in tg:
             g.close()
 
     # plans and graphs for every wave, built before the timed region
-    plans, graphs, tiles = [], [], 0
-    for lane, w in laned:
-        plan = Plan(items_for(gb, w, carve(bufs[lane], w)), threads=shape[0],
-                    ctas_per_sm=shape[1])
-        tiles += plan.tiles
-        s = streams[lane]
-        s.wait_stream(main)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=s):
-            plan.launch(s)
-        plans.append(plan)
-        graphs.append(graph)
-    torch.cuda.synchronize()
+    run = laned.LanedGraphs(laned_pairs, gb, fmts, lambda k, lane, w: bufs[lane],
+                            threads=shape[0], ctas_per_sm=shape[1])
+    tiles = run.tiles
 
     samples = sum(i.n_streams * i.n_per_stream for i in inst)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(main)
-    for s in streams:
-        s.wait_stream(main)
-    for (lane, _), graph in zip(laned, graphs):
-        with torch.cuda.stream(streams[lane]):
-            graph.replay()
-    for s in streams:
-        main.wait_stream(s)
+    run.replay()
     e1.record(main)
     torch.cuda.synchronize()
     b_ms = e0.elapsed_time(e1)
-    for plan in plans:
-        plan.close()
-    del graphs
+    run.close()
 
     # plain per-instance launches (one call per instance, one stream)
     gp = make_gens()
@@ -528,7 +673,7 @@ def run_batched(args):
     if not args.no_verify:
         vb, vp = make_gens(), make_gens()
         for w in waves:
-            ob, op = carve(bufs[0], w), carve(bufs[1], w)
+            ob, op = laned.carve(bufs[0], w, n_streams), laned.carve(bufs[1], w, n_streams)
             plan = Plan(items_for(vb, w, ob), threads=shape[0], ctas_per_sm=shape[1])
             plan.launch(main)
             for p, o in zip(w, op):
@@ -722,13 +867,47 @@ def _plain_rate(kind, n, steps, fmt, seed, reps=5):
 # adds 2 (a 64-bit add as add-with-carry).
 GEN_OPS = {0: 2, 1: 7, 2: 11}
 SUM_OPS = 2
-SMS, LANES_PER_SM_CLK = 152, 128  # 4 schedulers x 32 lanes issue per clock
+LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes issue per clock
+
+# The integer work of one output by operation class of the probes
+# (gbrng_probe_int): mwc_step = one 32 x 32 + 32 -> 64 multiply-add (two
+# instructions), lcg_mad = one 32-bit multiply-add, shift_xor = one shift and
+# one xor, add = one 32-bit add or a lone logic op.  xor128: t = x ^ (x << 11),
+# w ^ (w >> 19), ^ (t >> 8) are three shift-xors and ^ t a lone xor; KISS: the
+# MWC step, the LCG, xorshift32's three shift-xors and the two adds of the
+# sum.  FP32 output adds the shift of u >> 8 (the convert and the multiply run
+# on the floating-point pipes).
+OP_MIX = {0: {"mwc_step": 1}, 1: {"shift_xor": 3, "add": 1},
+          2: {"mwc_step": 1, "lcg_mad": 1, "shift_xor": 3, "add": 2}}
+F32_EXTRA = {"add": 1}
 
 
-def alu_peak_tops(mhz: float) -> float:
-    """Issue-limited integer rate: 152 SMs x 4 schedulers x 32 lanes per
-    clock, at the given SM clock."""
-    return SMS * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+def device_sms() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def alu_peak_tops(mhz: float, sms: int) -> float:
+    """Issue-limited integer rate: SMs x 4 schedulers x 32 lanes per clock,
+    at the given SM clock."""
+    return sms * LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+
+
+def int_roofline(kind: int, fmt: int, samples_per_s: float, probes: dict) -> dict:
+    """How much of the probed integer throughput a writeback kernel's
+    arithmetic uses: per operation class, samples/s x operations per sample
+    / the probe's operations/s for that class (the measured peak of the
+    pipe that runs it); `bound` is the class nearest its peak and `serial`
+    the sum over classes (the fraction if every class shared one pipe)."""
+    mix = dict(OP_MIX[kind])
+    if fmt == 1:
+        for c, v in F32_EXTRA.items():
+            mix[c] = mix.get(c, 0) + v
+    fr = {c: samples_per_s * v / probes[c]["ops_per_s"] for c, v in mix.items()}
+    bound = max(fr, key=fr.get)
+    return {"bound": bound, "frac": fr[bound], "serial": sum(fr.values()),
+            "classes": fr, "ops_per_sample": mix,
+            "peak_source": "gbrng_probe_int on this device, this run"}
 
 
 def _reduce_rate(kind, n, steps, op, seed, reps=5):
@@ -773,7 +952,7 @@ def _jump_ms(kind, n, k, seed, reps=5):
     return sorted(ts)[len(ts) // 2]
 
 
-def run_int_probes(clock_mhz: float):
+def run_int_probes(clock_mhz: float, sms: int):
     """Integer-pipe probes (gbrng_probe_int): 8 independent chains per
     thread of one operation, 1216 CTAs x 256 threads.  Returns, per op, the
     operations per second and the lane-instructions per SM per clock."""
@@ -782,7 +961,7 @@ def run_int_probes(clock_mhz: float):
     import torch
 
     from paper_1101_1846_gb300 import capi
-    blocks, threads, iters = SMS * 8, 256, 1 << 13
+    blocks, threads, iters = sms * 8, 256, 1 << 13
     sink = torch.empty(blocks * threads, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream()
     names = {0: ("mwc_step", 2), 1: ("lcg_mad", 1), 2: ("shift_xor", 2), 3: ("add", 1)}
@@ -801,7 +980,7 @@ def run_int_probes(clock_mhz: float):
         sec = a.elapsed_time(b) * 1e-3
         ops = blocks * threads * iters * 8 / sec
         res[name] = {"ops_per_s": ops, "instr_per_op": instr,
-                     "lane_instr_per_sm_clk": ops * instr / (SMS * clock_mhz * 1e6)}
+                     "lane_instr_per_sm_clk": ops * instr / (sms * clock_mhz * 1e6)}
     return res
 
 
@@ -814,10 +993,11 @@ def run_inline(clock_mhz: float):
 
     from paper_1101_1846_gb300 import capi
     n, steps = 1 << 22, 1024
-    peak = alu_peak_tops(clock_mhz)
+    sms = device_sms()
+    peak = alu_peak_tops(clock_mhz, sms)
     res = {"workload": f"2^22 streams x {steps} outputs, no output array",
-           "alu_peak_tops": peak, "alu_peak_basis": f"152 SMs x 128 lanes/clk x {clock_mhz} MHz",
-           "kinds": {}}
+           "alu_peak_tops": peak,
+           "alu_peak_basis": f"{sms} SMs x 128 lanes/clk x {clock_mhz} MHz", "kinds": {}}
     for kind in KINDS:
         r = _reduce_rate(kind, n, steps, capi.RNG_SUM_U32, 11)
         d = _reduce_rate(kind, n, steps, capi.RNG_DISC, 11)
@@ -828,7 +1008,7 @@ def run_inline(clock_mhz: float):
             "roofline": {"bound": "alu", "achieved": tops, "peak": peak, "unit": "Tops/s",
                          "frac": tops / peak, "ops_per_sample": ops},
             "jump_2^22_streams_by_2^40+1_ms": _jump_ms(kind, n, (1 << 40) + 1, 5)}
-    probes = run_int_probes(clock_mhz)
+    probes = run_int_probes(clock_mhz, sms)
     res["int_probes"] = probes
     mwc = res["kinds"]["mwc"]["sum_u32"]["gsamples_s"] * 1e9
     res["kinds"]["mwc"]["of_probed_mwc_step_rate"] = mwc / probes["mwc_step"]["ops_per_s"]

@@ -70,16 +70,18 @@ def loguniform_int(rng: np.random.Generator, lo: int, hi: int, size: int) -> np.
     return np.floor(lo * np.exp(u * np.log(hi / lo))).astype(np.int64)
 
 
-def batched_instances(count: int = 10_000, seed: int = 1234) -> list[Instance]:
+def batched_instances(count: int = 10_000, seed: int = 1234, streams_range=(32, 65536),
+                      steps_range=(16, 65536)) -> list[Instance]:
     """Uneven batched workload: kinds uniform over the three generators,
     stream counts log-uniform in [32, 65536], outputs per stream log-uniform
     in [16, 65536], uint32/FP32 drawn per instance, one seed per instance.
     Stream counts are not rounded, so about three quarters of the instances
-    take the scalar-store path."""
+    take the scalar-store path.  Smaller ranges give the same recipe scaled
+    down (for tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     kinds = rng.integers(0, 3, count)
-    streams = loguniform_int(rng, 32, 65536, count)
-    steps = loguniform_int(rng, 16, 65536, count)
+    streams = loguniform_int(rng, streams_range[0], streams_range[1], count)
+    steps = loguniform_int(rng, steps_range[0], steps_range[1], count)
     fmts = rng.integers(0, 2, count)
     seeds = rng.integers(0, 2**63, count, dtype=np.int64)
     return [Instance(int(kinds[i]), int(streams[i]), int(steps[i]), int(fmts[i]),
