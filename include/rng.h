@@ -411,16 +411,23 @@ int rng_generate_batch(const rng_batch_item *items, size_t n_items,
  * order they were submitted.  Results are the same whatever other requests
  * share the device (each is a function of its client and range only).
  *
- * The engine keeps submitted requests in a FIFO, admits a request when its
- * output fits in the device arena (the HBM budget minus the generators'
- * state), and on every tick runs one batched launch (a refilled plan) that
- * advances every client with admitted work by one piece of at most
- * chunk_rows rows of its current request: requests that arrive while others
- * run join the next tick (continuous batching).  Clients are split into two
+ * The engine keeps submitted requests in a FIFO and admits a request when
+ * its output fits in the device arena (the HBM budget minus the generators'
+ * state; first fit).  On every tick the engine runs one batched launch (a
+ * refilled plan) that advances every client with admitted work by one piece
+ * of at most chunk_rows rows of its sequence: the piece starts at the
+ * client's first unfinished request and runs on through the admitted
+ * requests after it, each request's part going to that request's output in
+ * its own format.  Requests that arrive while others run join the next tick
+ * (continuous batching); while a tick runs, a lane waits for a quarter of
+ * the target tick size (rng_server_set_tick_bytes) before it launches the
+ * next one.  Clients are split into two
  * lanes (even and odd ids) with a CUDA stream each, so that one lane's tick
  * overlaps the other's; up to two ticks per lane are in flight.  A request's output (uint32 or
  * float, N elements, contiguous, in sequence order) stays in the arena until
- * it is released.  Not thread-safe: drive one engine from one host thread.
+ * it is released; it starts at a word index congruent to its first sample's
+ * index in the client's sequence modulo 8 (so 4-byte aligned, and 16-byte
+ * aligned only when that index is a multiple of 4).  Not thread-safe: drive one engine from one host thread.
  * Paper: none; the parametrised generators of Sec. "Parallelizing RNGs"
  * served on demand.
  * ------------------------------------------------------------------- */
@@ -439,7 +446,8 @@ rng_server_handle rng_server_create(int kind, uint32_t n_clients,
 /* Queues a request for the next n_samples samples of `client` in format
  * fmt; *req_id receives its id (ids count up from 0).  The request's range
  * of the client's sequence is fixed here, at submission.  RNG_ERR_ARG for a
- * bad client or fmt, n_samples = 0, or an output larger than the arena. */
+ * bad client or fmt, n_samples = 0, or an output larger than the arena less
+ * the 28 bytes of room its placement may need. */
 int rng_server_submit(rng_server_handle s, uint32_t client, uint64_t n_samples, int fmt,
                       uint64_t *req_id);
 

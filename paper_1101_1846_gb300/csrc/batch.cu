@@ -29,17 +29,19 @@ namespace {
 enum TileMode : uint32_t { kTail = 0, kAligned = 1, kShifted = 2, kAlignedSync = 3 };
 
 struct Unit {
-    uint32_t *state;     // generator state (SoA, stride n)
-    const uint32_t *a;   // multipliers or nullptr
-    uint32_t *out;       // output element of stream s0 in row 0
-    uint64_t n;          // generator streams (state stride)
-    uint64_t ld;         // output row stride
-    uint64_t steps;      // outputs per stream (< 2^32)
-    uint32_t s0;         // first stream of the tile
-    uint32_t count;      // streams in the tile
-    uint32_t code;       // kind | fmt << 2 | mode << 3
-    uint32_t tail;       // shifted tiles: tail streams after the tile's (0-3)
+    uint32_t *state;       // generator state (SoA, stride n)
+    const uint32_t *a;     // multipliers or nullptr
+    uint32_t *out;         // output element of stream s0 in row 0
+    const uint32_t *fmap;  // mapped tiles: the output map (gen_body.cuh OutMap), else nullptr
+    uint64_t ld;           // output row stride
+    uint32_t n;            // generator streams (state stride; at most 2^30)
+    uint32_t steps;        // outputs per stream
+    uint32_t s0;           // first stream of the tile
+    uint32_t count;        // streams in the tile
+    uint32_t code;         // kind | fmt << 2 | mode << 3 (fmt unused in mixed tiles)
+    uint32_t tail;         // shifted tiles: tail streams after the tile's (0-3)
 };
+static_assert(sizeof(Unit) == 64, "a tile is one 64-byte record");
 
 // The scalar body with body_shift's barriers (one after the state loads,
 // then one every SYNC_ROWS rows of the blocks of four), so that one warp of a
@@ -51,11 +53,15 @@ template <int KIND, int FMT, int HINT>
 __device__ __forceinline__ void body_scalar_sync(uint32_t *__restrict__ state,
                                                  const uint32_t *__restrict__ mult, uint64_t n,
                                                  uint32_t steps, uint32_t *__restrict__ p0,
-                                                 uint64_t ld, uint64_t s, bool live)
+                                                 uint64_t ld, uint64_t s, bool live,
+                                                 const uint32_t *fmap = nullptr)
 {
     constexpr int W = KindTraits<KIND>::W;
     uint32_t w[kMaxWords][4] = {};
     uint32_t a[4] = {0, 0, 0, 0};
+    OutMap m;
+    if constexpr (FMT == kFmtMixed)
+        m.load(fmap);
     if (live) {
 #pragma unroll
         for (int k = 0; k < W; ++k)
@@ -67,22 +73,33 @@ __device__ __forceinline__ void body_scalar_sync(uint32_t *__restrict__ state,
     constexpr uint32_t every = KindTraits<KIND>::SYNC_ROWS / 4;
     const uint32_t blocks = steps / 4;
     uint32_t *p = p0;
-    for (uint32_t b = 0; b < blocks; ++b) {
-        if (b % every == 0)
-            __syncthreads();
+    if constexpr (FMT == kFmtMixed) {  // rolled: the mapped kernels stay small
+        for (uint32_t j = 0; j < steps; ++j) {
+            if (j % (4 * every) == 0 && j < 4 * blocks)
+                __syncthreads();
+            const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
+            if (live)
+                put4<FMT, HINT>(m, m.row(p), p, o);
+            p += ld;
+        }
+    } else {
+        for (uint32_t b = 0; b < blocks; ++b) {
+            if (b % every == 0)
+                __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
+                if (live)
+                    store4<HINT>(p, o);
+                p += ld;
+            }
+        }
+        for (uint32_t j = 4 * blocks; j < steps; ++j) {
             const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
             if (live)
                 store4<HINT>(p, o);
             p += ld;
         }
-    }
-    for (uint32_t j = 4 * blocks; j < steps; ++j) {
-        const uint32_t o = step_enc<KIND, FMT>(w, a, 0);
-        if (live)
-            store4<HINT>(p, o);
-        p += ld;
     }
     if (live) {
 #pragma unroll
@@ -95,15 +112,15 @@ template <int KIND, int FMT, int HINT>
 __device__ __forceinline__ void run_unit(const Unit &u)
 {
     const uint32_t mode = u.code >> 3;
-    const uint32_t steps = (uint32_t)u.steps;
+    const uint32_t steps = u.steps;
     const uint64_t c_first = 4 * (uint64_t)threadIdx.x;
     if (mode == kAligned) {
         if (c_first < u.count)
             body_vec<KIND, FMT, 1, HINT>(u.state, u.a, u.n, steps, u.out + c_first, u.ld,
-                                         u.s0 + c_first, 0);
+                                         u.s0 + c_first, 0, u.fmap);
     } else if (mode == kAlignedSync) {
         body_vec_sync<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c_first, u.ld,
-                                       u.s0 + c_first, c_first < u.count);
+                                       u.s0 + c_first, c_first < u.count, u.fmap);
     } else if (mode == kShifted) {
         // tail streams u.s0 + count .. + tail: the last warp, which then
         // holds no group (fill_units checks), with the same barriers
@@ -111,14 +128,15 @@ __device__ __forceinline__ void run_unit(const Unit &u)
         if (u.tail && warp == (blockDim.x >> 5) - 1)
             body_scalar_sync<KIND, FMT, HINT>(u.state, u.a, u.n, steps,
                                               u.out + u.count + lane, u.ld,
-                                              u.s0 + u.count + lane, lane < u.tail);
+                                              u.s0 + u.count + lane, lane < u.tail, u.fmap);
         else
             body_shift<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out, u.ld, u.s0,
-                                        u.count / 4);
+                                        u.count / 4, u.fmap);
     } else {
         const uint64_t c = threadIdx.x;
         if (c < u.count)
-            body_scalar<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c, u.ld, u.s0 + c);
+            body_scalar<KIND, FMT, HINT>(u.state, u.a, u.n, steps, u.out + c, u.ld, u.s0 + c,
+                                         u.fmap);
     }
 }
 
@@ -146,6 +164,41 @@ batch_kernel(const Unit *__restrict__ units, uint64_t n_units, unsigned long lon
         default: break;
         }
     }
+}
+
+// The persistent kernel of plans whose tiles carry output maps (the serving
+// engine's): the same bodies, with the place and format of every output
+// taken from its tile's map.  One kernel per kind (a plan of mapped tiles
+// holds one kind), so that each stays small enough for the instruction
+// cache and the plain batched kernel keeps its register count.
+template <int KIND, int HINT>
+__global__ void __launch_bounds__(512)
+batch_kernel_mixed(const Unit *__restrict__ units, uint64_t n_units, unsigned long long *next)
+{
+    __shared__ unsigned long long take;
+    for (;;) {
+        if (threadIdx.x == 0)
+            take = atomicAdd(next, 1ull);
+        __syncthreads();
+        const unsigned long long u = take;
+        __syncthreads();
+        if (u >= n_units)
+            return;
+        const Unit U = units[u];
+        run_unit<KIND, kFmtMixed, HINT>(U);
+    }
+}
+
+// Launches the mapped-tile kernel of `kind`.
+void launch_mixed(int kind, int grid, int threads, cudaStream_t st, const Unit *units,
+                  uint64_t n_units, unsigned long long *next)
+{
+    if (kind == RNG_MWC32)
+        batch_kernel_mixed<RNG_MWC32, 1><<<grid, threads, 0, st>>>(units, n_units, next);
+    else if (kind == RNG_XOR128)
+        batch_kernel_mixed<RNG_XOR128, 1><<<grid, threads, 0, st>>>(units, n_units, next);
+    else
+        batch_kernel_mixed<RNG_KISS, 1><<<grid, threads, 0, st>>>(units, n_units, next);
 }
 
 // CTA size when the caller passes 0: 512 was the fastest on GB300 for the
@@ -207,9 +260,10 @@ int validate_items(const rng_batch_item *items, size_t n_items, Claim *scratch, 
 }
 
 // Writes the tiles of every item to out[0 .. cap) (out may be null) and
-// returns how many there are.
+// returns how many there are.  maps (optional): item i's output format map
+// (a device pointer), given to each of its tiles.
 uint64_t fill_units(const rng_batch_item *items, size_t n_items, int threads, Unit *out,
-                    uint64_t cap)
+                    uint64_t cap, const uint32_t *const *maps = nullptr)
 {
     uint64_t count = 0;
     for (size_t i = 0; i < n_items; ++i) {
@@ -235,9 +289,10 @@ uint64_t fill_units(const rng_batch_item *items, size_t n_items, int threads, Un
                 u.state = g->d_state;
                 u.a = g->d_a;
                 u.out = base + c0;
-                u.n = g->n;
+                u.n = (uint32_t)g->n;
                 u.ld = r.ld;
-                u.steps = it.n_per_stream;
+                u.steps = (uint32_t)it.n_per_stream;
+                u.fmap = maps ? maps[i] : nullptr;
                 u.s0 = (uint32_t)(r.s_begin + c0);
                 u.count = (uint32_t)c;
                 u.code = (uint32_t)g->kind | ((uint32_t)it.fmt << 2) | (mode << 3);
@@ -275,13 +330,15 @@ void order_units(Unit *u, uint64_t n)
     });
 }
 
-int grid_for(int device, int threads, int ctas_per_sm, int *grid)
+int grid_for(int device, int threads, int ctas_per_sm, int *grid, bool mixed = false)
 {
     int sms = 0, fit = 0;
     int st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     if (!st)
-        st = cuda_status(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel<kHint>, threads, 0));
+        st = cuda_status(mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                     &fit, batch_kernel_mixed<RNG_KISS, kHint>, threads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                     &fit, batch_kernel<kHint>, threads, 0));
     if (!st) {
         fit = std::max(fit, 1);
         *grid = sms * (ctas_per_sm ? std::min(ctas_per_sm, fit) : fit);
@@ -306,6 +363,16 @@ struct Plan {
     uint64_t pinned_cap[2] = {0, 0};
     cudaEvent_t copied[2] = {nullptr, nullptr};
     int turn = 0;
+    // output format maps of mixed tiles (plan_refill_mixed): device copy and
+    // two pinned host lists used in turn with the tile lists
+    bool mixed = false;  // the current tiles carry maps: batch_kernel_mixed runs them
+    int mixed_kind = 0;  // their kind (one per mapped refill)
+    int ctas_per_sm = 0;
+    int grid_mixed = 0;
+    uint32_t *d_maps = nullptr;
+    uint64_t cap_maps = 0;  // words
+    uint32_t *pinned_maps[2] = {nullptr, nullptr};
+    uint64_t pinned_maps_cap[2] = {0, 0};
 };
 
 void free_plan(Plan *p)
@@ -318,9 +385,11 @@ void free_plan(Plan *p)
             cudaEventDestroy(p->copied[k]);
         }
         cudaFreeHost(p->pinned[k]);
+        cudaFreeHost(p->pinned_maps[k]);
     }
     cudaFree(p->d_units);
     cudaFree(p->d_next);
+    cudaFree(p->d_maps);
     delete p;
 }
 
@@ -360,6 +429,7 @@ extern "C" rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n
     if (!st) {
         p->device = device;
         p->threads = threads;
+        p->ctas_per_sm = ctas_per_sm;
         p->n_units = units.size();
         st = grid_for(device, threads, ctas_per_sm, &p->grid);
     }
@@ -396,7 +466,12 @@ extern "C" int rng_plan_launch(rng_plan_handle h, void *cuda_stream)
         cudaSetDevice(p->device);
     int status = cuda_status(cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), st));
     if (!status) {
-        batch_kernel<kHint><<<p->grid, p->threads, 0, st>>>(p->d_units, p->n_units, p->d_next);
+        if (p->mixed)
+            launch_mixed(p->mixed_kind, p->grid_mixed, p->threads, st, p->d_units, p->n_units,
+                         p->d_next);
+        else
+            batch_kernel<kHint><<<p->grid, p->threads, 0, st>>>(p->d_units, p->n_units,
+                                                               p->d_next);
         status = cuda_status(cudaGetLastError());
     }
     if (prev >= 0 && prev != p->device)
@@ -404,11 +479,54 @@ extern "C" int rng_plan_launch(rng_plan_handle h, void *cuda_stream)
     return status;
 }
 
-extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, size_t n_items,
-                               void *cuda_stream)
+namespace gbrng {
+namespace {
+
+// Grows a pinned host list to at least `need` elements (keeps no contents).
+template <class T>
+int ensure_pinned(T **buf, uint64_t *cap, uint64_t need, uint64_t other_cap)
 {
-    Plan *p = reinterpret_cast<Plan *>(h);
-    if (!p || !items || n_items == 0)
+    if (need <= *cap)
+        return RNG_OK;
+    cudaFreeHost(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    const uint64_t want = std::max<uint64_t>(need, 2 * other_cap);
+    if (cudaHostAlloc(reinterpret_cast<void **>(buf), want * sizeof(T), cudaHostAllocDefault) !=
+        cudaSuccess)
+        return set_error(RNG_ERR_OOM);
+    *cap = want;
+    return RNG_OK;
+}
+
+// Grows a device buffer to at least `need` elements (at least doubling, so
+// that lists of varying length settle after a few ticks: the free below
+// synchronises the device); waits first for work on `stream` that may
+// still read the old one.
+template <class T>
+int ensure_device(T **buf, uint64_t *cap, uint64_t need, cudaStream_t stream)
+{
+    if (need <= *cap)
+        return RNG_OK;
+    const uint64_t want = std::max<uint64_t>(need, 2 * *cap);
+    int st = cuda_status(cudaStreamSynchronize(stream));
+    T *grown = nullptr;
+    if (!st && cudaMalloc(&grown, want * sizeof(T)) != cudaSuccess)
+        st = set_error(RNG_ERR_OOM);
+    if (!st) {
+        cudaFree(*buf);
+        *buf = grown;
+        *cap = want;
+    }
+    return st;
+}
+
+// The refill of rng_plan_refill and plan_refill_mixed: with `maps` (host
+// words) every item i gets the map at word map_off[i] of them.
+int refill(Plan *p, const rng_batch_item *items, size_t n_items, const uint64_t *map_off,
+           const uint32_t *maps, uint64_t map_words, cudaStream_t stream)
+{
+    if (!p || !items || n_items == 0 || (maps && (!map_off || map_words == 0)))
         return set_error(RNG_ERR_ARG);
     int device = -1;
     p->claims.resize(n_items);
@@ -417,42 +535,48 @@ extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, s
         return st;
     if (device != p->device)
         return set_error(RNG_ERR_ARG);
+    int kind = -1;  // a mapped refill holds one kind (its kernel carries one)
+    if (maps)
+        for (size_t i = 0; i < n_items; ++i) {
+            const int k = reinterpret_cast<Gen *>(items[i].h)->kind;
+            if (map_off[i] + 3 >= map_words || (kind >= 0 && k != kind))
+                return set_error(RNG_ERR_ARG);
+            kind = k;
+        }
     const uint64_t n = fill_units(items, n_items, p->threads, nullptr, 0);
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->device)
         cudaSetDevice(p->device);
     const int k = p->turn;
-    if (p->copied[k])  // the copy out of this list, two refills ago
+    if (p->copied[k])  // the copies out of this turn's lists, two refills ago
         st = cuda_status(cudaEventSynchronize(p->copied[k]));
     else
         st = cuda_status(cudaEventCreateWithFlags(&p->copied[k], cudaEventDisableTiming));
-    if (!st && n > p->pinned_cap[k]) {
-        cudaFreeHost(p->pinned[k]);
-        p->pinned[k] = nullptr;
-        p->pinned_cap[k] = 0;
-        const uint64_t cap = std::max<uint64_t>(n, 2 * p->pinned_cap[k ^ 1]);
-        if (cudaHostAlloc(reinterpret_cast<void **>(&p->pinned[k]), cap * sizeof(Unit),
-                          cudaHostAllocDefault) != cudaSuccess)
-            st = set_error(RNG_ERR_OOM);
-        else
-            p->pinned_cap[k] = cap;
-    }
     if (!st)
-        fill_units(items, n_items, p->threads, p->pinned[k], n);
-    if (!st && n > p->cap_units) {
-        // grow: wait for work that may still read the old list
-        st = cuda_status(cudaStreamSynchronize(stream));
-        Unit *grown = nullptr;
-        if (!st && cudaMalloc(&grown, n * sizeof(Unit)) != cudaSuccess)
-            st = set_error(RNG_ERR_OOM);
+        st = ensure_pinned(&p->pinned[k], &p->pinned_cap[k], n, p->pinned_cap[k ^ 1]);
+    if (!st)
+        st = ensure_device(&p->d_units, &p->cap_units, n, stream);
+    std::vector<const uint32_t *> dmaps;
+    if (!st && maps) {
+        st = ensure_pinned(&p->pinned_maps[k], &p->pinned_maps_cap[k], map_words,
+                           p->pinned_maps_cap[k ^ 1]);
+        if (!st)
+            st = ensure_device(&p->d_maps, &p->cap_maps, map_words, stream);
+        if (!st && !p->grid_mixed)
+            st = grid_for(p->device, p->threads, p->ctas_per_sm, &p->grid_mixed, true);
         if (!st) {
-            cudaFree(p->d_units);
-            p->d_units = grown;
-            p->cap_units = n;
+            dmaps.resize(n_items);
+            for (size_t i = 0; i < n_items; ++i)
+                dmaps[i] = p->d_maps + map_off[i];
+            std::memcpy(p->pinned_maps[k], maps, map_words * sizeof(uint32_t));
+            st = cuda_status(cudaMemcpyAsync(p->d_maps, p->pinned_maps[k],
+                                             map_words * sizeof(uint32_t),
+                                             cudaMemcpyHostToDevice, stream));
         }
     }
+    if (!st)
+        fill_units(items, n_items, p->threads, p->pinned[k], n, maps ? dmaps.data() : nullptr);
     if (!st && n)
         st = cuda_status(cudaMemcpyAsync(p->d_units, p->pinned[k], n * sizeof(Unit),
                                          cudaMemcpyHostToDevice, stream));
@@ -460,11 +584,33 @@ extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, s
         st = cuda_status(cudaEventRecord(p->copied[k], stream));
     if (!st) {
         p->n_units = n;
+        p->mixed = maps != nullptr;
+        p->mixed_kind = kind;
         p->turn ^= 1;
     }
     if (prev >= 0 && prev != p->device)
         cudaSetDevice(prev);
     return st;
+}
+
+}  // namespace
+
+int plan_refill_mixed(rng_plan_handle h, const rng_batch_item *items, size_t n_items,
+                      const uint64_t *map_off, const uint32_t *maps, uint64_t map_words,
+                      cudaStream_t stream)
+{
+    if (!maps)
+        return set_error(RNG_ERR_ARG);
+    return refill(reinterpret_cast<Plan *>(h), items, n_items, map_off, maps, map_words, stream);
+}
+
+}  // namespace gbrng
+
+extern "C" int rng_plan_refill(rng_plan_handle h, const rng_batch_item *items, size_t n_items,
+                               void *cuda_stream)
+{
+    return refill(reinterpret_cast<Plan *>(h), items, n_items, nullptr, nullptr, 0,
+                  static_cast<cudaStream_t>(cuda_stream));
 }
 
 extern "C" uint64_t rng_plan_tiles(rng_plan_handle h)

@@ -121,6 +121,22 @@ inline bool mont_table(int kind) { return kind == RNG_MWC32 || kind == RNG_KISS;
 // Kinds that need the device jump tables (GF(2) or affine parts).
 inline bool needs_jump_tables(int kind) { return kind != RNG_MWC32 && kind != RNG_MWC16X2; }
 
+// Mapped tiles of the batched kernel: each output's format and place come
+// from its tile's output map (gen_body.cuh, OutMap).  kFmtMixed is the
+// format value of such tiles; kFmtEnd ends a map.
+constexpr int kFmtMixed = 2;
+constexpr uint32_t kFmtEnd = 0xFFFFFFFFu;
+
+// batch.cu: refills a plan (rng_plan_refill) with tiles whose outputs are
+// placed and encoded by output maps (OutMap layout, in host words `maps`;
+// item i's map starts at word map_off[i], its origin a device address), and
+// makes its launches run the mapped-tile kernel.  The items' fmt fields are
+// ignored; each item's out pointer is its place in the map's virtual window.
+// Same rules and errors as rng_plan_refill.
+int plan_refill_mixed(rng_plan_handle p, const rng_batch_item *items, size_t n_items,
+                      const uint64_t *map_off, const uint32_t *maps, uint64_t map_words,
+                      cudaStream_t stream);
+
 // Handles with at most this many streams keep a split scratch (split calls
 // only happen for stream counts well below it).
 constexpr uint64_t kSplitMaxStreams = (uint64_t)1 << 19;

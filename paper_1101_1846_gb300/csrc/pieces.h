@@ -38,4 +38,39 @@ inline void piece_items(rng_handle h, uint64_t n, uint64_t c, uint64_t m, uint32
     columns(rem, n, q);
 }
 
+// Splits items[first ..) at multiples of 8 streams, where that makes their
+// middles 32-byte aligned: an item whose row stride is a multiple of 8 and
+// whose output of stream s sits at a word address congruent to s modulo 8
+// (the serving engine places every output so) becomes up to three items: the
+// streams before the first multiple of 8, the streams from there to the last
+// multiple of 8 (aligned rows: the batched kernel's barrier-free vector
+// tiles), and the rest.  Other items stay as they are.  The stream ranges
+// stay disjoint and every output keeps its place.
+inline void split_aligned(std::vector<rng_batch_item> &items, size_t first)
+{
+    const size_t end = items.size();
+    for (size_t i = first; i < end; ++i) {
+        const rng_batch_item it = items[i];
+        const uint64_t w = (uint64_t)(reinterpret_cast<uintptr_t>(it.out) / 4);
+        if (it.ld % 8 != 0 || (w - it.s_begin) % 8 != 0)
+            continue;
+        const uint64_t a = std::min((it.s_begin + 7) / 8 * 8, it.s_end);
+        const uint64_t b = std::max(a, it.s_end / 8 * 8);
+        if (b == a || (a == it.s_begin && b == it.s_end))
+            continue;  // nothing aligned to split off, or aligned already
+        auto part = [&](uint64_t s0, uint64_t s1) {
+            rng_batch_item q = it;
+            q.s_begin = s0;
+            q.s_end = s1;
+            q.out = static_cast<uint32_t *>(it.out) + (s0 - it.s_begin);
+            return q;
+        };
+        items[i] = part(a, b);
+        if (it.s_begin < a)
+            items.push_back(part(it.s_begin, a));
+        if (b < it.s_end)
+            items.push_back(part(b, it.s_end));
+    }
+}
+
 }  // namespace gbrng

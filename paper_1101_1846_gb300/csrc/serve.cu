@@ -11,6 +11,13 @@
 // Each column range maps to at most two contiguous stream ranges (the window
 // wraps around stream n-1), so a piece is at most four batch items with
 // disjoint stream ranges of one generator, all in the same launch.
+//
+// One piece per client and tick runs through several of its requests: the
+// kernel writes the piece as one virtual window of the client's sequence and
+// the piece's output map (runs.h, gen_body.cuh) sends each request's part to
+// that request's output in its format.  Every output is placed at a word
+// index congruent to its first sample's index modulo 8, so that all of a
+// client's outputs agree with any window of its sequence modulo 32 bytes.
 #include <algorithm>
 #include <deque>
 #include <new>
@@ -19,6 +26,7 @@
 
 #include "arena.h"
 #include "pieces.h"
+#include "runs.h"
 #include "gbrng.cuh"
 
 namespace gbrng {
@@ -29,16 +37,32 @@ constexpr int kMaxInflight = 2;     // ticks in flight per lane
 constexpr int kLanes = 2;           // client c belongs to lane c % kLanes
 constexpr int kServeThreads = 512;
 
+// Arena bytes of a request of n samples: its output and room to place it at
+// the word phase of its first sample (placement_pad).
+inline uint64_t block_bytes(uint64_t n) { return 4 * n + 4 * (kPhaseWords - 1); }
+
+
 struct Req {
     uint32_t client = 0;
     uint64_t n = 0;      // samples
     int fmt = 0;
     uint64_t start = 0;  // first sample index in the client's sequence
-    uint64_t off = 0;    // arena byte offset
-    uint64_t done = 0;   // samples already scheduled
+    uint64_t off = 0;    // arena byte offset of the output
+    uint64_t block = 0;  // the arena block that holds it (see placement_pad)
     bool admitted = false;
     bool completed = false;
     double done_ms = 0;
+};
+
+// An admitted request as the ticks see it (kept beside its client's others,
+// so that building a tick reads no hash map).
+struct Act {
+    uint64_t id;
+    uint64_t off;    // arena byte offset
+    uint64_t n;      // samples
+    uint64_t done;   // samples already scheduled
+    uint64_t start;  // first sample index in the client's sequence
+    int fmt;
 };
 
 struct Tick {
@@ -57,12 +81,15 @@ struct Server {
     Arena *arena = nullptr;
     std::vector<uint64_t> cursor;                 // next sample index per client
     std::deque<uint64_t> pending;                 // waiting for admission
-    std::vector<std::deque<uint64_t>> active;     // admitted, per client, in order
+    std::vector<std::deque<Act>> active;          // admitted, per client, in order
     std::unordered_map<uint64_t, Req> reqs;
     std::deque<Tick> inflight[kLanes];
     std::vector<cudaEvent_t> spare_events;
     std::deque<std::pair<uint64_t, double>> done;  // completed, not yet taken
     std::vector<rng_batch_item> items;
+    std::vector<uint64_t> item_map;  // per item: word offset of its piece's format map
+    std::vector<uint32_t> maps;      // the tick's format maps
+    std::vector<RunReq> run;         // a client's active requests, for run_piece
     rng_plan_handle plan[kLanes] = {};
     cudaStream_t stream[kLanes] = {};
     cudaEvent_t t0 = nullptr;
@@ -118,15 +145,64 @@ void admit(Server *S)
 {
     while (!S->pending.empty()) {
         Req &q = S->reqs[S->pending.front()];
-        uint64_t off = 0;
-        if (!S->arena->alloc(q.n * 4, &off))
+        uint64_t block = 0;
+        if (!S->arena->alloc(block_bytes(q.n), &block))
             break;  // first come, first served: later requests wait too
-        q.off = off;
+        q.block = block;
+        q.off = block + placement_pad(block, q.start);
         q.admitted = true;
-        S->active[q.client].push_back(S->pending.front());
+        S->active[q.client].push_back(Act{S->pending.front(), q.off, q.n, 0, q.start, q.fmt});
         S->pending.pop_front();
         ++S->n_admitted;
     }
+}
+
+// Rows per client in the next tick of `lane`: an equal share of the target
+// tick for every busy client, at most chunk_rows (chunk_rows alone when no
+// target is set).
+uint64_t tick_rows(const Server *S, int lane)
+{
+    uint64_t rows = S->chunk_rows;
+    if (S->tick_bytes) {
+        uint64_t busy = 0;
+        for (uint32_t c = lane; c < S->n_clients; c += kLanes)
+            busy += !S->active[c].empty();
+        const uint64_t share = busy ? S->tick_bytes / (busy * S->streams * 4) : rows;
+        rows = std::max<uint64_t>(1, std::min<uint64_t>(rows, share));
+    }
+    return rows;
+}
+
+// Client c's piece of a tick of at most cap samples: its front request and
+// the ones after it (run_piece).
+RunPiece client_piece(Server *S, uint32_t c, uint64_t cap)
+{
+    const std::deque<Act> &act = S->active[c];
+    S->run.clear();
+    uint64_t have = 0;  // samples the collected requests still need
+    for (size_t i = 0; i < act.size() && have < cap; ++i) {
+        const Act &q = act[i];
+        S->run.push_back(RunReq{q.off, q.n, q.done, q.fmt});
+        have += q.n - q.done;
+    }
+    return run_piece(S->run.data(), S->run.size(), cap);
+}
+
+// a piece's window indices stay below 2^31 (format maps are 32-bit)
+uint64_t piece_cap(const Server *S, uint64_t rows)
+{
+    return std::min<uint64_t>(rows * S->streams, 1ull << 31);
+}
+
+// Samples the next tick of `lane` would write.
+uint64_t tick_samples(Server *S, int lane)
+{
+    const uint64_t cap = piece_cap(S, tick_rows(S, lane));
+    uint64_t total = 0;
+    for (uint32_t c = lane; c < S->n_clients; c += kLanes)
+        if (!S->active[c].empty())
+            total += client_piece(S, c, cap).m;
+    return total;
 }
 
 // One tick of `lane`: one piece of every busy client of the lane, one launch
@@ -134,17 +210,10 @@ void admit(Server *S)
 int launch_tick(Server *S, int lane)
 {
     S->items.clear();
+    S->item_map.clear();
+    S->maps.clear();
     Tick tick;
-    uint64_t rows = S->chunk_rows;
-    if (S->tick_bytes) {
-        // an equal share of the target tick for every client with work
-        uint64_t busy = 0;
-        for (uint32_t c = lane; c < S->n_clients; c += kLanes)
-            busy += !S->active[c].empty();
-        const uint64_t share = busy ? S->tick_bytes / (busy * S->streams * 4) : rows;
-        rows = std::max<uint64_t>(1, std::min<uint64_t>(rows, share));
-    }
-    const uint64_t cap = rows * S->streams;
+    const uint64_t cap = piece_cap(S, tick_rows(S, lane));
     // clients lane, lane + kLanes, ... (none when the lane is past the last client)
     const uint32_t per_lane =
         (uint32_t)lane < S->n_clients ? (S->n_clients - lane + kLanes - 1) / kLanes : 0;
@@ -152,30 +221,55 @@ int launch_tick(Server *S, int lane)
         const uint32_t c = lane + kLanes * ((S->rr[lane] + k) % per_lane);
         if (S->active[c].empty())
             continue;
-        const uint64_t id = S->active[c].front();
-        Req &q = S->reqs[id];
-        const uint64_t m = std::min(q.n - q.done, cap);
-        uint32_t *out = S->arena_base + q.off / 4 + q.done;
-        piece_items(S->gens[c], S->streams, q.start + q.done, m, out, q.fmt, S->items);
-        q.done += m;
-        S->samples += m;
-        if (q.done == q.n) {
-            tick.completing.push_back(id);
-            S->active[c].pop_front();
+        std::deque<Act> &act = S->active[c];
+        const RunPiece pc = client_piece(S, c, cap);
+        const Act &q0 = act.front();
+        // the piece's output map: origin, then (start, format, shift) per
+        // segment, then the end entry
+        const uint64_t map_at = S->maps.size();
+        const uintptr_t origin = reinterpret_cast<uintptr_t>(S->arena_base + pc.origin);
+        S->maps.push_back((uint32_t)(origin & 0xFFFFFFFFu));
+        S->maps.push_back((uint32_t)((uint64_t)origin >> 32));
+        for (const Seg &g : pc.segs) {
+            S->maps.push_back(g.b);
+            S->maps.push_back((uint32_t)g.fmt);
+            S->maps.push_back((uint32_t)((uint64_t)g.shift & 0xFFFFFFFFu));
+            S->maps.push_back((uint32_t)((uint64_t)g.shift >> 32));
         }
+        S->maps.insert(S->maps.end(), {kFmtEnd, 0u, 0u, 0u});
+        const size_t first = S->items.size();
+        piece_items(S->gens[c], S->streams, q0.start + q0.done, pc.m,
+                    S->arena_base + pc.origin, RNG_U32, S->items);
+        split_aligned(S->items, first);
+        S->item_map.resize(S->items.size(), map_at);
+        // the requests the piece completes, and how far it reaches into the last
+        uint64_t left = pc.m;
+        for (size_t j = 0; j < pc.touched; ++j) {
+            Act &q = act.front();
+            const uint64_t take = std::min(q.n - q.done, left);
+            q.done += take;
+            left -= take;
+            if (q.done < q.n)
+                break;
+            tick.completing.push_back(q.id);
+            act.pop_front();
+        }
+        S->samples += pc.m;
     }
     if (per_lane)
         S->rr[lane] = (S->rr[lane] + 1) % per_lane;
     if (S->items.empty())
         return RNG_OK;
-    int st;
+    int st = RNG_OK;
     if (!S->plan[lane]) {
         S->plan[lane] = rng_plan_create(S->items.data(), S->items.size(), S->plan_threads,
                                         S->plan_ctas);
         st = S->plan[lane] ? RNG_OK : rng_last_error();
-    } else {
-        st = rng_plan_refill(S->plan[lane], S->items.data(), S->items.size(), S->stream[lane]);
     }
+    if (!st)
+        st = plan_refill_mixed(S->plan[lane], S->items.data(), S->items.size(),
+                               S->item_map.data(), S->maps.data(), S->maps.size(),
+                               S->stream[lane]);
     if (!st)
         st = rng_plan_launch(S->plan[lane], S->stream[lane]);
     if (st)
@@ -228,6 +322,12 @@ int progress(Server *S)
     admit(S);
     for (int ln = 0; ln < kLanes; ++ln) {
         while ((int)S->inflight[ln].size() < kMaxInflight && lane_active(S, ln)) {
+            // with a tick already running, wait for enough work to make the
+            // next one worth a launch: a tick takes a client's whole adjacent
+            // run, so one launched at once would often hold a few bytes
+            if (!S->inflight[ln].empty() && S->tick_bytes &&
+                4 * tick_samples(S, ln) < S->tick_bytes / 4)
+                break;
             st = launch_tick(S, ln);
             if (st)
                 return st;
@@ -334,7 +434,7 @@ extern "C" int rng_server_submit(rng_server_handle h, uint32_t client, uint64_t 
 {
     Server *S = reinterpret_cast<Server *>(h);
     if (!S || client >= S->n_clients || n_samples == 0 || (fmt != RNG_U32 && fmt != RNG_F32) ||
-        n_samples > S->arena->size() / 4)
+        block_bytes(n_samples) > S->arena->size())
         return set_error(RNG_ERR_ARG);
     const uint64_t id = S->next_id++;
     Req q;
@@ -359,7 +459,8 @@ extern "C" int rng_server_submit_many(rng_server_handle h, const uint32_t *clien
         return set_error(RNG_ERR_ARG);
     for (size_t i = 0; i < n; ++i)  // all or nothing
         if (clients[i] >= S->n_clients || n_samples[i] == 0 ||
-            (fmts[i] != RNG_U32 && fmts[i] != RNG_F32) || n_samples[i] > S->arena->size() / 4)
+            (fmts[i] != RNG_U32 && fmts[i] != RNG_F32) ||
+            block_bytes(n_samples[i]) > S->arena->size())
             return set_error(RNG_ERR_ARG);
     for (size_t i = 0; i < n; ++i) {
         int st = rng_server_submit(h, clients[i], n_samples[i], fmts[i], req_ids ? &req_ids[i]
@@ -474,7 +575,7 @@ extern "C" int rng_server_release(rng_server_handle h, uint64_t req_id)
     auto it = S->reqs.find(req_id);
     if (it == S->reqs.end() || !it->second.completed)
         return set_error(RNG_ERR_ARG);
-    S->arena->release(it->second.off, it->second.n * 4);
+    S->arena->release(it->second.block, block_bytes(it->second.n));
     S->reqs.erase(it);
     return RNG_OK;
 }

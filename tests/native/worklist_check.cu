@@ -51,7 +51,7 @@ int main()
     for (const Unit &u : units) {
         const uint64_t item = ((uintptr_t)u.state >> 32) - 1;
         std::printf("%" PRIu64 " %u %u %u %u %td %" PRIu64 "\n", item, u.code >> 3, u.s0,
-                    u.count, u.tail, u.out - base, u.steps);
+                    u.count, u.tail, u.out - base, (uint64_t)u.steps);
     }
     return 0;
 }

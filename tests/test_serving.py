@@ -90,7 +90,10 @@ def test_mixed_requests_equal_oracle_and_alone():
     outs = run_all(mixed, log)
     check_against_oracle(mixed, log, outs, oracle.KISS, n)
     st = mixed.stats()
-    assert st["completed"] == len(log) and st["ticks"] > len(log) // clients
+    # a tick advances each client by at most chunk_rows * n samples
+    per_client = [sum(r.n_samples for r in log if r.client == c) for c in range(clients)]
+    assert st["completed"] == len(log)
+    assert st["ticks"] >= max(-(-t // (2 * n)) for t in per_client)
     mixed.close()
     alone = Server(capi.RNG_KISS, clients, n, seed_base=77, budget_bytes=64 << 20,
                    chunk_rows=2)
@@ -98,6 +101,28 @@ def test_mixed_requests_equal_oracle_and_alone():
     for i in outs:
         assert np.array_equal(outs[i][1], outs2[i][1]), i
     alone.close()
+
+
+SIZES = [5, 1, 2000, 3, 1003, 1004, 7, 4096, 9, 1, 1, 2, 333, 1, 64]
+
+
+@pytest.mark.parametrize("kind,n", [(oracle.KISS, 1003), (oracle.KISS, 1024), (oracle.KISS, 3),
+                                    (oracle.MWC, 1001), (oracle.XOR128, 1000)])
+def test_one_piece_spans_requests_of_mixed_formats(kind, n):
+    """Many small requests of one client, formats alternating request by
+    request (requests of one sample put two format changes inside one
+    16-byte store), all admitted at once: their outputs sit back to back in
+    the arena, so one piece of the client's sequence runs through all of them
+    in a single tick, its format map flipping at every request boundary; and
+    every output equals the oracle's."""
+    log = [workloads.Request(0.0, 0, size, i % 2) for i, size in enumerate(SIZES * 3)]
+    total = sum(r.n_samples for r in log)
+    rows = -(-total // n)
+    s = Server(kind, 1, n, seed_base=5, budget_bytes=64 << 20, chunk_rows=rows)
+    outs = run_all(s, log)
+    check_against_oracle(s, log, outs, kind, n)
+    assert s.stats()["ticks"] == 1
+    s.close()
 
 
 @pytest.mark.parametrize("kind", [oracle.MWC, oracle.XOR128])
@@ -159,7 +184,7 @@ def test_drain_reports_blocked_admission():
     s = Server(capi.RNG_XOR128, 1, n, seed_base=2, budget_bytes=n * 16 + (1 << 20) + 8192,
                chunk_rows=8)
     arena = s.stats()["arena_size"]
-    a = s.submit(0, arena // 4, 0)  # fills the arena
+    a = s.submit(0, (arena - 28) // 4, 0)  # fills the arena (28 bytes of placement room)
     b = s.submit(0, 1024, 0)
     with pytest.raises(capi.RngError):
         s.drain()  # b cannot be admitted until a is released

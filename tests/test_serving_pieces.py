@@ -42,16 +42,32 @@ def cases():
     return out
 
 
-def test_items_cover_the_piece_exactly_once(pieces_bin):
+@pytest.mark.parametrize("split", [0, 1])
+def test_items_cover_the_piece_exactly_once(pieces_bin, split):
+    """With split = 1 the items are also cut at multiples of 8 streams
+    (split_aligned), the window placed at word phase c mod 8 as the serving
+    engine places outputs: still every sample once, and for n a multiple of
+    8 every item of 8 or more streams that starts at a multiple of 8 has
+    32-byte aligned rows, and no other item holds a whole aligned block of 8
+    streams."""
     cs = cases()
-    r = subprocess.run([str(pieces_bin)], input="".join(f"{n} {c} {m}\n" for n, c, m in cs),
+    r = subprocess.run([str(pieces_bin)],
+                       input="".join(f"{n} {c} {m} {split}\n" for n, c, m in cs),
                        capture_output=True, text=True, check=True, timeout=120)
     lines = r.stdout.strip().split("\n")
     assert len(lines) == len(cs)
     for (n, c, m), line in zip(cs, lines):
         v = [int(x) for x in line.split()]
         count, items = v[0], [v[1 + 5 * i: 6 + 5 * i] for i in range(v[0])]
-        assert 1 <= count <= 4, (n, c, m)
+        assert 1 <= count <= (12 if split else 4), (n, c, m)
+        if split and n % 8 == 0:
+            for s_begin, s_end, rows, off, ld in items:
+                # stream s's output sits at window offset off + (s - s_begin),
+                # word phase (c + off) mod 8 at the item's first stream
+                if s_begin % 8 == 0 and s_end - s_begin >= 8:
+                    assert (c + off - s_begin) % 8 == 0 and (s_end - s_begin) % 8 == 0
+                else:  # nothing aligned left in it to split off
+                    assert s_end // 8 * 8 <= (s_begin + 7) // 8 * 8, (n, c, m, s_begin, s_end)
         covered = np.zeros(m, dtype=np.int64)
         ranges = []
         for s_begin, s_end, rows, off, ld in items:
