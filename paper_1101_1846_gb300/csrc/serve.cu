@@ -65,6 +65,16 @@ struct Act {
     int fmt;
 };
 
+// A request waiting for admission (its client and size beside its id, so
+// that the admission scan reads no hash map); id kGone once admitted past
+// the head.
+constexpr uint64_t kGone = ~0ull;
+struct Pend {
+    uint64_t id;
+    uint64_t n;
+    uint32_t client;
+};
+
 struct Tick {
     cudaEvent_t ev = nullptr;
     std::vector<uint64_t> completing;
@@ -80,7 +90,12 @@ struct Server {
     uint32_t *arena_base = nullptr;
     Arena *arena = nullptr;
     std::vector<uint64_t> cursor;                 // next sample index per client
-    std::deque<uint64_t> pending;                 // waiting for admission
+    std::deque<Pend> pending;  // waiting for admission, in order (admitted
+                               // entries past the head are marked kGone)
+    size_t n_pending = 0;      // entries not marked
+    uint64_t bypassed = 0;        // bytes admitted past the waiting head
+    bool rescan = true;           // space released or requests queued since the last scan
+    std::vector<char> held;       // admission scan: clients with a request waiting
     std::vector<std::deque<Act>> active;          // admitted, per client, in order
     std::unordered_map<uint64_t, Req> reqs;
     std::deque<Tick> inflight[kLanes];
@@ -141,19 +156,59 @@ int retire(Server *S)
     return RNG_OK;
 }
 
+// Requests after a waiting head that admission looks at, per call.
+constexpr size_t kLookahead = 1024;
+
+bool admit_one(Server *S, uint64_t id)
+{
+    Req &q = S->reqs[id];
+    uint64_t block = 0;
+    if (!S->arena->alloc(block_bytes(q.n), &block))
+        return false;
+    q.block = block;
+    q.off = block + placement_pad(block, q.start);
+    q.admitted = true;
+    S->active[q.client].push_back(Act{id, q.off, q.n, 0, q.start, q.fmt});
+    ++S->n_admitted;
+    return true;
+}
+
+// First come, first served; when the head waits for space (a large output
+// and a fragmented arena), later requests of other clients may go first,
+// each client's requests still in order (a client with a waiting request
+// admits none after it), until the bytes admitted past the head reach half
+// the arena: then admission waits for the head, so that it cannot starve.
 void admit(Server *S)
 {
     while (!S->pending.empty()) {
-        Req &q = S->reqs[S->pending.front()];
-        uint64_t block = 0;
-        if (!S->arena->alloc(block_bytes(q.n), &block))
-            break;  // first come, first served: later requests wait too
-        q.block = block;
-        q.off = block + placement_pad(block, q.start);
-        q.admitted = true;
-        S->active[q.client].push_back(Act{S->pending.front(), q.off, q.n, 0, q.start, q.fmt});
+        if (S->pending.front().id != kGone) {
+            if (!admit_one(S, S->pending.front().id))
+                break;
+            --S->n_pending;
+            S->bypassed = 0;
+        }
         S->pending.pop_front();
-        ++S->n_admitted;
+    }
+    if (S->pending.empty() || S->bypassed >= S->arena->size() / 2 || !S->rescan)
+        return;
+    S->rescan = false;  // nothing can change until space is released or work queued
+    S->held.assign(S->n_clients, 0);
+    S->held[S->pending.front().client] = 1;
+    size_t seen = 0;
+    for (size_t k = 1; k < S->pending.size() && seen < kLookahead &&
+                       S->bypassed < S->arena->size() / 2;
+         ++k, ++seen) {
+        Pend &q = S->pending[k];
+        if (q.id == kGone)
+            continue;
+        if (!S->held[q.client] && block_bytes(q.n) <= S->arena->largest() &&
+            admit_one(S, q.id)) {
+            S->bypassed += block_bytes(q.n);
+            q.id = kGone;
+            --S->n_pending;
+        } else {
+            S->held[q.client] = 1;
+        }
     }
 }
 
@@ -444,7 +499,9 @@ extern "C" int rng_server_submit(rng_server_handle h, uint32_t client, uint64_t 
     q.start = S->cursor[client];
     S->cursor[client] += n_samples;
     S->reqs.emplace(id, q);
-    S->pending.push_back(id);
+    S->pending.push_back(Pend{id, n_samples, client});
+    ++S->n_pending;
+    S->rescan = true;
     if (req_id)
         *req_id = id;
     return RNG_OK;
@@ -492,7 +549,7 @@ extern "C" int rng_server_drain(rng_server_handle h)
         if (st)
             return st;
         if (!any_inflight(S)) {
-            if (S->pending.empty() && !has_active(S))
+            if (S->n_pending == 0 && !has_active(S))
                 return RNG_OK;
             if (!has_active(S))
                 return set_error(RNG_ERR_BUSY);  // waiting requests need released space
@@ -576,6 +633,7 @@ extern "C" int rng_server_release(rng_server_handle h, uint64_t req_id)
     if (it == S->reqs.end() || !it->second.completed)
         return set_error(RNG_ERR_ARG);
     S->arena->release(it->second.block, block_bytes(it->second.n));
+    S->rescan = true;
     S->reqs.erase(it);
     return RNG_OK;
 }
@@ -605,7 +663,7 @@ extern "C" int rng_server_stats(rng_server_handle h, uint64_t *out8)
     out8[4] = S->samples;
     out8[5] = S->arena->used();
     out8[6] = S->arena->size();
-    out8[7] = S->pending.size();
+    out8[7] = S->n_pending;
     return RNG_OK;
 }
 

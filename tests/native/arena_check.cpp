@@ -1,7 +1,8 @@
 // Drives the serving arena (paper_1101_1846_gb300/csrc/arena.h) from a
 // script on stdin: "size granule" first, then "a BYTES" (alloc: prints
 // "1 OFFSET" or "0 0") and "r OFFSET BYTES" (release: prints the bytes in
-// use), so that a test can compare it with a model.
+// use, the free blocks and the largest of them), so that a test can compare
+// it with a model.
 #include <cinttypes>
 #include <cstdio>
 
@@ -27,7 +28,7 @@ int main()
             if (std::scanf("%" SCNu64 " %" SCNu64, &off, &bytes) != 2)
                 return 2;
             a.release(off, bytes);
-            std::printf("%" PRIu64 " %zu\n", a.used(), a.free_blocks());
+            std::printf("%" PRIu64 " %zu %" PRIu64 "\n", a.used(), a.free_blocks(), a.largest());
         } else {
             return 2;
         }

@@ -79,7 +79,8 @@ def test_arena_matches_first_fit_model(arena_bin, seed):
             b = live.pop(off)
             model.release(off, b)
             ops.append(f"r {off} {b}")
-            expect.append(("r", model.used, len(model.free)))
+            expect.append(("r", model.used, len(model.free),
+                           max((ln for _, ln in model.free), default=0)))
         else:
             b = int(np.exp(rng.random() * np.log(8 << 20))) + 1  # 1 B .. 8 MiB, log-uniform
             off = model.alloc(b)
@@ -99,8 +100,8 @@ def test_arena_matches_first_fit_model(arena_bin, seed):
             off, used = vals
             assert got == ([1, off, used] if off is not None else [0, 0, used]), i
         else:
-            used, blocks = vals
-            assert got == [used, blocks], i
+            used, blocks, largest = vals
+            assert got == [used, blocks, largest], i
 
 
 def test_arena_release_merges_to_one_block(arena_bin):
@@ -111,7 +112,7 @@ def test_arena_release_merges_to_one_block(arena_bin):
                        text=True, check=True, timeout=60)
     lines = r.stdout.split("\n")
     assert [lines[i].split()[1] for i in (1, 2, 3, 4)] == ["0", "1024", "2048", "3072"]
-    assert lines[5].split() == [str(3 * 1024), "2"]   # a hole at 1024, the tail after 4096
-    assert lines[6].split() == [str(2 * 1024), "2"]   # 0 merges with 1024
-    assert lines[7].split() == [str(1024), "2"]       # 3072 merges with the tail
-    assert lines[8].split() == ["0", "1"]             # everything one free block again
+    assert lines[5].split()[:2] == [str(3 * 1024), "2"]   # a hole at 1024, the tail after 4096
+    assert lines[6].split()[:2] == [str(2 * 1024), "2"]   # 0 merges with 1024
+    assert lines[7].split()[:2] == [str(1024), "2"]       # 3072 merges with the tail
+    assert lines[8].split() == ["0", "1", str(size)]  # everything one free block again

@@ -179,6 +179,34 @@ def test_admission_waits_for_budget():
     s.close()
 
 
+def test_admission_looks_past_a_waiting_head():
+    """Client 0's second large request waits for space; client 1's small
+    requests behind it are admitted at once (each client's requests still in
+    order), and every output equals the oracle's."""
+    n, clients = 512, 2
+    s = Server(capi.RNG_KISS, clients, n, seed_base=4,
+               budget_bytes=clients * n * 20 + (1 << 20) + 8192, chunk_rows=4)
+    arena = s.stats()["arena_size"]
+    big, small = int(0.6 * arena) // 4, int(0.1 * arena) // 4
+    log = [workloads.Request(0.0, 0, big, 0), workloads.Request(0.0, 0, big, 1),
+           workloads.Request(0.0, 1, small, 1), workloads.Request(0.0, 1, small, 0)]
+    rids = [s.submit(r.client, r.n_samples, r.fmt) for r in log]
+    s.progress()
+    st = s.stats()
+    assert st["admitted"] == 3 and st["waiting"] == 1  # only the second large one waits
+    outs = {}
+    while len(outs) < len(rids):
+        s.progress()
+        for rid, _ in s.take():
+            outs[rid] = s.copy(rid).cpu().numpy().view(np.uint32)
+            s.release(rid)
+    starts = [0, big, 0, small]
+    check_against_oracle(s, log, {i: ({"client": r.client, "n": r.n_samples,
+                                        "start": starts[i]}, outs[rids[i]])
+                                   for i, r in enumerate(log)}, oracle.KISS, n)
+    s.close()
+
+
 def test_drain_reports_blocked_admission():
     n = 256
     s = Server(capi.RNG_XOR128, 1, n, seed_base=2, budget_bytes=n * 16 + (1 << 20) + 8192,
