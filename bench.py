@@ -512,20 +512,31 @@ def run_ours(args):
         del out
         torch.cuda.empty_cache()
         host, placement = pinned_near_gpu(torch, (steps, n), local)
-        # the link itself: a plain device-to-host copy of (up to) 1 GiB into
-        # the same pinned buffer, best of three
+        # the link itself: plain device-to-host copies into the same pinned
+        # buffer, (a) 1 GiB at its start, best of three, and (b) the whole
+        # buffer in 256 MiB pieces from one device buffer, the bytes and
+        # pattern of one host-delivery call
         m = min(1 << 28, host.numel())
         src = torch.empty(m, dtype=torch.int32, device="cuda")
-        dst = host.view(-1)[:m]
+        flat = host.view(-1)
         link = []
         for _ in range(4):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dst.copy_(src, non_blocking=True)
+            flat[:m].copy_(src, non_blocking=True)
             b.record(stream)
             b.synchronize()
             link.append(a.elapsed_time(b))
         link_gbs = 4 * m / (min(link[1:]) * 1e-3) / 1e9
+        piece = min(1 << 26, flat.numel())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for off in range(0, flat.numel(), piece):
+            k = min(piece, flat.numel() - off)
+            flat[off:off + k].copy_(src[:k], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        link_full_gbs = 4 * flat.numel() / (a.elapsed_time(b) * 1e-3) / 1e9
         del src
         for k, f in pairs[:1]:
             gens[k].generate_host(steps, f, out=host)  # warm-up (staging buffers)
@@ -544,8 +555,10 @@ def run_ours(args):
                "steps": args.e2e_steps,
                "api": "rng_generate_host into pinned host memory",
                "d2h_gbs": len(pairs) * n * steps * 4 * args.e2e_steps / dt / 1e9,
-               "plain_copy_d2h_gbs": link_gbs, "host_buffer": placement}
+               "plain_copy_d2h_gbs": link_gbs, "plain_copy_whole_buffer_d2h_gbs": link_full_gbs,
+               "host_buffer": placement}
         e2e["of_plain_copy"] = e2e["d2h_gbs"] / link_gbs
+        e2e["of_plain_copy_whole_buffer"] = e2e["d2h_gbs"] / link_full_gbs
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -582,6 +595,27 @@ def run_ours(args):
         sat = line.get("serving", {}).get("saturating")
         if sat:
             sat["over_plain_full_device"] = sat["gsamples_s"] / value
+        # a compact summary of the other workloads inside the roofline entry,
+        # each rate as a fraction of the copy peak (4 bytes per sample plus
+        # the state, as the roofline counts them)
+        summary = {}
+        for name, r in line.get("other_configs", {}).items():
+            kname, _, rest = name.partition("_")
+            k = {v: i for i, v in KNAME.items()}[kname]
+            nn, ss = (1 << 20, 1024) if "2^20" in rest else (4096, 4096)
+            gbs = alg_bytes(k, nn, ss) / (r["ms"] * 1e-3) / 1e9
+            summary[name] = {"gsamples_s": round(r["gsamples_s"], 1),
+                             "frac": round(gbs / peak, 3)}
+        if "batched" in line:
+            summary["batched_10000"] = {
+                "gsamples_s": round(line["batched"]["value"], 1),
+                "over_plain_full_device": round(line["batched"]["over_plain_full_device"], 3)}
+        if sat:
+            summary["serving_saturating"] = {
+                "gsamples_s": round(sat["gsamples_s"], 1),
+                "over_plain_full_device": round(sat["over_plain_full_device"], 3)}
+        if summary:
+            line["roofline"]["configs"] = summary
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

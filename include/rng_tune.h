@@ -25,6 +25,12 @@ extern "C" {
 int gbrng_set_launch(int kind, int fmt, int v, int block, int hint);
 int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
 
+/* The same per size class: class 0 holds the shapes of calls of fewer than
+ * 2^21 streams, class 1 those of the rest (the class gbrng_set_launch and
+ * gbrng_get_launch address).  Returns 0 or RNG_ERR_ARG. */
+int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, int block, int hint);
+int gbrng_get_launch_class(int kind, int fmt, int size_class, int *v, int *block, int *hint);
+
 /* Sequence splitting of few-stream calls (rng_generate, rng_generate_reduce):
  * `log2_rows` is log2 of the fewest rows a segment may have for `kind`
  * (1..30); 0 turns splitting off for the kind.  A split generate call takes

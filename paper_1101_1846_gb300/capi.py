@@ -116,6 +116,9 @@ SIGNATURES = {
     "rng_last_error": (ctypes.c_int, []),
     "rng_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gbrng_set_launch": (ctypes.c_int, [ctypes.c_int] * 5),
+    "gbrng_set_launch_class": (ctypes.c_int, [ctypes.c_int] * 6),
+    "gbrng_get_launch_class": (ctypes.c_int, [ctypes.c_int] * 3 +
+                               [ctypes.POINTER(ctypes.c_int)] * 3),
     "gbrng_get_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] +
                          [ctypes.POINTER(ctypes.c_int)] * 3),
     "gbrng_set_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),

@@ -75,7 +75,8 @@ struct LaunchShape {
     int block;  // CTA size
     int hint;   // streaming stores
 };
-LaunchShape launch_shape(int kind, int fmt);
+// The shape for a call of `streams` streams (its size class).
+LaunchShape launch_shape(int kind, int fmt, uint64_t streams);
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st);
 // generate_paper.cu: the same for RNG_MWC16X2, RNG_XORSHIFT8, RNG_KISS_XOR.
 int launch_generate_paper(int kind, int fmt, const GenLaunch &p, cudaStream_t st);

@@ -329,7 +329,7 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
     const uint64_t count = p.s_end - p.s_begin;
     if (p.steps == 0 || count == 0)
         return RNG_OK;
-    const LaunchShape sh = launch_shape(KIND, fmt);
+    const LaunchShape sh = launch_shape(KIND, fmt, count);
     Fn vec, shift, sync;
     if (fmt == RNG_F32) {
         pick_vec<KIND, RNG_F32>(sh.v, sh.hint, vec);

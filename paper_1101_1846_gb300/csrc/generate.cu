@@ -21,14 +21,30 @@ struct Shape {
 // forms measured the same, and KISS and XORSHIFT8, whose steps cost more,
 // ran 4-40 % slower that way.  Per-warp bulk copies of 512 B (each warp
 // staging its own rows, no block barrier) were slower than both.
-Shape g_shape[kKinds][2] = {
-    {{1, 256, 2}, {2, 256, 1}},  // MWC u32, f32
-    {{1, 256, 2}, {1, 128, 1}},  // xor128
-    {{2, 512, 1}, {2, 512, 1}},  // KISS
-    {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
-    {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
-    {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
+//
+// Two size classes: calls of fewer than kSmallStreams streams (class 0) and
+// the rest (class 1).  At 2^20 streams x 1024 the FP32 forms fill the GPU
+// differently: xor128 FP32 ran 1345 GS/s with its 2^22 shape (1, 128) and
+// 1608 with (2, 128); KISS FP32 1580 with (2, 512) and 1789 with (1, 256).
+Shape g_shape[2][kKinds][2] = {
+    {
+        {{1, 256, 2}, {2, 512, 1}},  // MWC u32, f32
+        {{1, 256, 2}, {2, 128, 1}},  // xor128
+        {{2, 512, 1}, {1, 256, 1}},  // KISS
+        {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
+        {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
+        {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
+    },
+    {
+        {{1, 256, 2}, {2, 256, 1}},  // MWC u32, f32
+        {{1, 256, 2}, {1, 128, 1}},  // xor128
+        {{2, 512, 1}, {2, 512, 1}},  // KISS
+        {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
+        {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
+        {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
+    },
 };
+constexpr uint64_t kSmallStreams = (uint64_t)1 << 21;
 
 // Fewest rows of a split segment, as log2, per kind (0: never split).  The
 // jump that starts a segment costs about as much as this many rows: MWC32 a
@@ -49,9 +65,9 @@ constexpr uint64_t kSplitFillThreads = (uint64_t)kSMs * 2048;
 
 }  // namespace
 
-LaunchShape launch_shape(int kind, int fmt)
+LaunchShape launch_shape(int kind, int fmt, uint64_t streams)
 {
-    const Shape s = g_shape[kind][fmt];
+    const Shape s = g_shape[streams < kSmallStreams ? 0 : 1][kind][fmt];
     return LaunchShape{s.v, s.block, s.hint};
 }
 
@@ -102,14 +118,34 @@ int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
 
 }  // namespace gbrng
 
-extern "C" int gbrng_set_launch(int kind, int fmt, int v, int block, int hint)
+extern "C" int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, int block,
+                                      int hint)
 {
     using namespace gbrng;
-    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || (v != 1 && v != 2) || block < 32 ||
-        block > 512 || (block & (block - 1)) || hint < 0 || hint > 2)
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || size_class < 0 || size_class > 1 ||
+        (v != 1 && v != 2) || block < 32 || block > 512 || (block & (block - 1)) || hint < 0 ||
+        hint > 2)
         return set_error(RNG_ERR_ARG);
-    g_shape[kind][fmt] = Shape{v, block, hint};
+    g_shape[size_class][kind][fmt] = Shape{v, block, hint};
     return RNG_OK;
+}
+
+extern "C" int gbrng_get_launch_class(int kind, int fmt, int size_class, int *v, int *block,
+                                      int *hint)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || size_class < 0 || size_class > 1 ||
+        !v || !block || !hint)
+        return set_error(RNG_ERR_ARG);
+    *v = g_shape[size_class][kind][fmt].v;
+    *block = g_shape[size_class][kind][fmt].block;
+    *hint = g_shape[size_class][kind][fmt].hint;
+    return RNG_OK;
+}
+
+extern "C" int gbrng_set_launch(int kind, int fmt, int v, int block, int hint)
+{
+    return gbrng_set_launch_class(kind, fmt, 1, v, block, hint);
 }
 
 extern "C" int gbrng_set_split(int kind, int log2_rows)
@@ -132,11 +168,5 @@ extern "C" int gbrng_get_split(int kind, int *log2_rows)
 
 extern "C" int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint)
 {
-    using namespace gbrng;
-    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || !v || !block || !hint)
-        return set_error(RNG_ERR_ARG);
-    *v = g_shape[kind][fmt].v;
-    *block = g_shape[kind][fmt].block;
-    *hint = g_shape[kind][fmt].hint;
-    return RNG_OK;
+    return gbrng_get_launch_class(kind, fmt, 1, v, block, hint);
 }

@@ -82,6 +82,24 @@ def test_launch_shape_roundtrip(lib):
     assert lib.gbrng_set_launch(2, 1, *old) == 0
 
 
+def test_launch_shape_classes(lib):
+    """Class 1 is what gbrng_set_launch / gbrng_get_launch address; class 0
+    (calls of fewer than 2^21 streams) is separate."""
+    v, b, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ref = (ctypes.byref(v), ctypes.byref(b), ctypes.byref(h))
+    assert lib.gbrng_get_launch_class(1, 1, 0, *ref) == 0
+    small = (v.value, b.value, h.value)
+    assert lib.gbrng_get_launch_class(1, 1, 1, *ref) == 0
+    large = (v.value, b.value, h.value)
+    assert lib.gbrng_set_launch(1, 1, 2, 64, 0) == 0
+    lib.gbrng_get_launch_class(1, 1, 1, *ref)
+    assert (v.value, b.value, h.value) == (2, 64, 0)
+    lib.gbrng_get_launch_class(1, 1, 0, *ref)
+    assert (v.value, b.value, h.value) == small
+    assert lib.gbrng_set_launch_class(1, 1, 2, 1, 64, 0) == capi.RNG_ERR_ARG
+    assert lib.gbrng_set_launch(1, 1, *large) == 0
+
+
 def test_no_device_reports_nodev(lib):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

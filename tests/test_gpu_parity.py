@@ -2,6 +2,7 @@
 uint32 and for the FP32 uniforms, which are exact by construction."""
 from __future__ import annotations
 
+import ctypes
 import functools
 import hashlib
 import json
@@ -203,17 +204,23 @@ def test_batch_disjoint_ranges_of_one_handle():
 
 
 def test_launch_shapes_do_not_change_outputs():
+    """Shapes of the small-call class (fewer than 2^21 streams, which n is)."""
     n, steps, seed = 4096, 21, 3
     exp = {k: expect_full(k, n, seed, steps, oracle.F32)[0] for k in KINDS}
-    saved = {k: autotune.get_shape(k, oracle.F32) for k in KINDS}
+    L = capi.lib()
+    saved = {}
+    for k in KINDS:
+        vals = [ctypes.c_int() for _ in range(3)]
+        capi.check(L.gbrng_get_launch_class(k, oracle.F32, 0, *[ctypes.byref(x) for x in vals]))
+        saved[k] = [x.value for x in vals]
     for v, block, hint in [(1, 64, 0), (2, 128, 1), (2, 512, 0), (1, 512, 1), (2, 32, 0)]:
         for k in KINDS:
-            capi.check(capi.lib().gbrng_set_launch(k, oracle.F32, v, block, hint))
+            capi.check(L.gbrng_set_launch_class(k, oracle.F32, 0, v, block, hint))
             out = Generator(k, n, seed).generate(steps, oracle.F32)
             torch.cuda.synchronize()
             assert np.array_equal(bits(out), obits(exp[k])), (k, v, block, hint)
     for k in KINDS:
-        autotune.set_shape(k, oracle.F32, saved[k])
+        capi.check(L.gbrng_set_launch_class(k, oracle.F32, 0, *saved[k]))
 
 
 # --------------------------------------------------------- the workloads
