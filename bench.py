@@ -61,6 +61,10 @@ def parse():
                    help="serving: target output per tick, shared by busy clients")
     p.add_argument("--sat-tick-gib", type=float, default=32.0,
                    help="serving, saturating run: target output per tick (throughput)")
+    p.add_argument("--budget-gib", type=float, default=40.0,
+                   help="serving: HBM budget (state plus outputs)")
+    p.add_argument("--saturating-only", action="store_true",
+                   help="serving: only the saturating run (no real-time run, no check pass)")
     p.add_argument("--instances", type=int, default=10_000)
     p.add_argument("--wave-gib", type=float, default=24.0)
     p.add_argument("--tune", action="store_true", help="autotune launch shapes first")
@@ -512,6 +516,11 @@ def run_ours(args):
         del out
         torch.cuda.empty_cache()
         host, placement = pinned_near_gpu(torch, (steps, n), local)
+        # warm-up: one untimed step of every pair (staging buffers, and the first
+        # passes over a freshly pinned buffer, which reach host memory slowly)
+        for k, f in pairs:
+            gens[k].generate_host(steps, f, out=host)
+        torch.cuda.synchronize()
         # the link itself: plain device-to-host copies into the same pinned
         # buffer, (a) 1 GiB at its start, best of three, and (b) the whole
         # buffer in 256 MiB pieces from one device buffer, the bytes and
@@ -538,16 +547,27 @@ def run_ours(args):
         b.synchronize()
         link_full_gbs = 4 * flat.numel() / (a.elapsed_time(b) * 1e-3) / 1e9
         del src
-        for k, f in pairs[:1]:
-            gens[k].generate_host(steps, f, out=host)  # warm-up (staging buffers)
-        torch.cuda.synchronize()
         barrier()
+        per_pair = {p: 0.0 for p in pairs}
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             for k, f in pairs:
-                gens[k].generate_host(steps, f, out=host)
+                tp = time.perf_counter()
+                gens[k].generate_host(steps, f, out=host)  # synchronous
+                per_pair[(k, f)] += time.perf_counter() - tp
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        # the link again, after the timed region (the host's memory is shared)
+        src = torch.empty(piece, dtype=torch.int32, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for off in range(0, flat.numel(), piece):
+            k = min(piece, flat.numel() - off)
+            flat[off:off + k].copy_(src[:k], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        link_after_gbs = 4 * flat.numel() / (a.elapsed_time(b) * 1e-3) / 1e9
+        del src
         dt = replicas.max_over_ranks(dt, device="cuda")
         e2e_samples = world * args.e2e_steps * len(pairs) * n * steps
         e2e = {"value": e2e_samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -556,6 +576,10 @@ def run_ours(args):
                "api": "rng_generate_host into pinned host memory",
                "d2h_gbs": len(pairs) * n * steps * 4 * args.e2e_steps / dt / 1e9,
                "plain_copy_d2h_gbs": link_gbs, "plain_copy_whole_buffer_d2h_gbs": link_full_gbs,
+               "plain_copy_whole_buffer_after_d2h_gbs": link_after_gbs,
+               "per_pair_d2h_gbs": {f"{KNAME[k]}_{FNAME[f]}":
+                                    round(4 * n * steps * args.e2e_steps / t / 1e9, 1)
+                                    for (k, f), t in per_pair.items()},
                "host_buffer": placement}
         e2e["of_plain_copy"] = e2e["d2h_gbs"] / link_gbs
         e2e["of_plain_copy_whole_buffer"] = e2e["d2h_gbs"] / link_full_gbs
@@ -788,7 +812,7 @@ def run_serving(args):
     golden = json.loads((ROOT / "tests" / "golden" / "multipliers_b32.json").read_text())
     chunk_rows = args.serve_chunk_rows
     server = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
-                    budget_bytes=40 << 30, chunk_rows=chunk_rows,
+                    budget_bytes=int(args.budget_gib * (1 << 30)), chunk_rows=chunk_rows,
                     tick_bytes=int(args.tick_gib * (1 << 30)))
     totals = {}
     for r in log:
@@ -823,28 +847,39 @@ def run_serving(args):
             if not np.array_equal(got, exp):
                 bad[0] += 1
 
-    live = replay(server, log, realtime=True).summary()
-    server.close()
+    if args.saturating_only:
+        server.close()
+        probes = None
+        live = None
+    else:
+        live = replay(server, log, realtime=True).summary()
+        server.close()
     # saturating run: the same requests, all submitted at once, with the
     # engine's tick sized for throughput (after a short warm-up engine)
     sat_tick = int(args.sat_tick_gib * (1 << 30))
     warm = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
-                  budget_bytes=40 << 30, chunk_rows=chunk_rows, tick_bytes=sat_tick)
+                  budget_bytes=int(args.budget_gib * (1 << 30)), chunk_rows=chunk_rows, tick_bytes=sat_tick)
     replay(warm, log[:2000], realtime=False)
     warm.close()
     server2 = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
-                     budget_bytes=40 << 30, chunk_rows=chunk_rows, tick_bytes=sat_tick)
+                     budget_bytes=int(args.budget_gib * (1 << 30)), chunk_rows=chunk_rows, tick_bytes=sat_tick)
     sat = replay(server2, log, realtime=False).summary()
     sat["tick_bytes"] = sat_tick
     server2.close()
     # untimed check: the same requests again, probing every k-th result
     if probes is not None:
         server3 = Server(capi.RNG_KISS, n_clients, streams, seed_base=args.seed,
-                         budget_bytes=40 << 30, chunk_rows=chunk_rows,
+                         budget_bytes=int(args.budget_gib * (1 << 30)), chunk_rows=chunk_rows,
                     tick_bytes=int(args.tick_gib * (1 << 30)))
         active.append(server3)
         replay(server3, log, realtime=False, on_done=on_done)
         server3.close()
+    if live is None:
+        return {"metric": METRIC, "workload": "serving_saturating", "impl": "ours",
+                "value": sat["gsamples_s"], "unit": UNIT, "saturating": sat,
+                "config": {"clients": n_clients, "streams_per_client": streams,
+                           "duration_s": args.duration, "budget_bytes":
+                           int(args.budget_gib * (1 << 30)), "tick_bytes": sat_tick}}
     line = {
         "metric": METRIC, "workload": "serving", "impl": "ours",
         "value": live["gsamples_s"], "unit": UNIT,
@@ -856,7 +891,8 @@ def run_serving(args):
         "max_arena_used_bytes": live["max_arena_used"], "ticks": live["ticks"],
         "config": {"workload": "serving", "clients": n_clients, "streams_per_client": streams,
                    "kind": "kiss", "rate_hz": args.rate, "duration_s": args.duration,
-                   "sizes": "log-uniform [1 KiB, 256 MiB]", "budget_bytes": 40 << 30,
+                   "sizes": "log-uniform [1 KiB, 256 MiB]",
+                   "budget_bytes": int(args.budget_gib * (1 << 30)),
                    "chunk_rows": chunk_rows, "tick_bytes": int(args.tick_gib * (1 << 30)),
                    "seed_base": args.seed},
     }
