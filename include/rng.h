@@ -253,11 +253,10 @@ int rng_generate_reduce(rng_handle h, uint64_t n_per_stream, int op, void *out);
  * it (Sec. "Parallelizing RNGs"). */
 int rng_jump(rng_handle h, uint64_t k);
 
-/* Most birthday-spacings samples rng_battery takes: at 512 days in a year
- * of 2^24 the repeat count's mean is about 0.3 % below the Poisson limit of
- * 2 it is compared with, a bias that millions of samples would detect but
- * a few thousand cannot (DIEHARD takes a few hundred). */
-#define RNG_BATTERY_BIRTHDAY_MAX 4096
+/* Most birthday-spacings samples rng_battery takes (2^21, a bound on the
+ * work; the statistics compare the repeat counts with their distribution at
+ * 512 days in a year of 2^24, which holds at millions of samples). */
+#define RNG_BATTERY_BIRTHDAY_MAX ((uint64_t)1 << 21)
 
 /* Counts of a small statistical battery (rng_battery). */
 typedef struct rng_battery_counts {

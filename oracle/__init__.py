@@ -132,7 +132,7 @@ def _load(path: Path):
         "oracle_bat_ones": (u64, [_u32p, u64]),
         "oracle_bat_bytes": (None, [_u32p, u64, _u64p]),
         "oracle_bat_serial": (None, [_u32p, u64, u64, _u64p]),
-        "oracle_bat_birthday": (u64, [_u32p, u64, u64, _u64p]),
+        "oracle_bat_birthday": (u64, [_u32p, u64, u64, u64, _u64p]),
         "oracle_mwc_period": (u64, [u32, u32, u32, i32, u64]),
         "oracle_xorshift32_period": (u64, [u32]),
         "oracle_lcg_period": (u64, [u32]),
@@ -411,9 +411,13 @@ def lcg_jump(z: int, k: int) -> int:
 
 
 # --------------------------------------------------------------- battery
-def battery_counts(u: np.ndarray) -> dict:
+BIRTHDAY_MAX = 1 << 21  # oracle.h's ORACLE_BAT_BIRTHDAY_MAX
+
+
+def battery_counts(u: np.ndarray, birthday_max: int = BIRTHDAY_MAX) -> dict:
     """Counts of the four battery tests over u of shape (n_per_stream,
-    n_streams), stream-interleaved uint32."""
+    n_streams), stream-interleaved uint32; at most birthday_max birthday
+    samples."""
     u = np.ascontiguousarray(u, dtype=np.uint32)
     rows, n = u.shape
     byte, serial, bday = (np.zeros(256, np.uint64), np.zeros(256, np.uint64),
@@ -422,7 +426,7 @@ def battery_counts(u: np.ndarray) -> dict:
     ones = int(L.oracle_bat_ones(_p32(u), u.size))
     L.oracle_bat_bytes(_p32(u), u.size, _p64(byte))
     L.oracle_bat_serial(_p32(u), n, rows, _p64(serial))
-    samples = int(L.oracle_bat_birthday(_p32(u), n, rows, _p64(bday)))
+    samples = int(L.oracle_bat_birthday(_p32(u), n, rows, birthday_max, _p64(bday)))
     return {"n_outputs": int(u.size), "ones": ones, "bytes": byte, "serial": serial,
             "birthday_samples": samples, "birthday": bday}
 

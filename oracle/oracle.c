@@ -872,22 +872,18 @@ static int cmp_u32(const void *x, const void *y)
  * the top 24 bits of 512 consecutive outputs of one stream.  Sort them; the
  * spacings are the first birthday and the differences of neighbours (m
  * values); sort the spacings; the statistic is the number of spacings equal
- * to the one before them.  It is asymptotically Poisson with mean
- * m^3 / (4 * 2^24) = 2; at m = 512 triple coincidences pull the exact mean
- * about 0.3 % lower, which enough samples would resolve, so at most
- * ORACLE_BAT_BIRTHDAY_MAX samples are taken (DIEHARD takes a few hundred).
- * Sample i is block i / n_streams (512 outputs) of stream i % n_streams,
- * for i below min(floor(n_per_stream / 512) * n_streams, the cap); hist[k]
- * counts samples with k repeats, k < 15, and hist[15] those with 15 or
- * more.  Returns the number of samples. */
+ * to the one before them.  Sample i is block i / n_streams (512 outputs) of
+ * stream i % n_streams, for i below min(floor(n_per_stream / 512) *
+ * n_streams, max_samples); hist[k] counts samples with k repeats, k < 15,
+ * and hist[15] those with 15 or more.  Returns the number of samples. */
 uint64_t oracle_bat_birthday(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
-                             uint64_t hist[16])
+                             uint64_t max_samples, uint64_t hist[16])
 {
     uint32_t b[512], d[512];
     uint64_t samples = 0;
     memset(hist, 0, 16 * sizeof(uint64_t));
     for (uint64_t blk = 0; (blk + 1) * 512 <= n_per_stream; ++blk)
-        for (uint64_t s = 0; s < n_streams && samples < ORACLE_BAT_BIRTHDAY_MAX; ++s) {
+        for (uint64_t s = 0; s < n_streams && samples < max_samples; ++s) {
             for (int i = 0; i < 512; ++i)
                 b[i] = u[(blk * 512 + i) * n_streams + s] >> 8;
             qsort(b, 512, sizeof(uint32_t), cmp_u32);

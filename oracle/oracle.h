@@ -101,9 +101,9 @@ uint64_t oracle_bat_ones(const uint32_t *u, uint64_t count);
 void oracle_bat_bytes(const uint32_t *u, uint64_t count, uint64_t hist[256]);
 void oracle_bat_serial(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
                        uint64_t hist[256]);
-#define ORACLE_BAT_BIRTHDAY_MAX 4096
+#define ORACLE_BAT_BIRTHDAY_MAX ((uint64_t)1 << 21)
 uint64_t oracle_bat_birthday(const uint32_t *u, uint64_t n_streams, uint64_t n_per_stream,
-                             uint64_t hist[16]);
+                             uint64_t max_samples, uint64_t hist[16]);
 
 /* brute-force periods (pins) */
 uint64_t oracle_mwc_period(uint32_t a, uint32_t x0, uint32_t c0, int log2b,

@@ -8,7 +8,8 @@ kind, not a replacement.
   monobit    z = (ones - 16 N) / sqrt(8 N), two-sided normal p-value
   frequency  chi-square of the 256 top-byte bins, 255 degrees of freedom
   serial     chi-square of the 256 pair cells, 255 degrees of freedom
-  birthday   chi-square of the samples' repeat counts against Poisson(2),
+  birthday   chi-square of the samples' repeat counts against their
+             distribution at m = 512 days in a year of n = 2^24 (birthday_pmf),
              bins 0..6 and >= 7, 7 degrees of freedom
 """
 from __future__ import annotations
@@ -22,7 +23,49 @@ import torch
 from . import capi
 from .generator import Generator
 
-BIRTHDAY_MEAN = 512 ** 3 / (4 * 2 ** 24)  # = 2
+BIRTHDAY_DAYS, BIRTHDAY_YEAR = 512, 1 << 24
+
+
+def birthday_moments(m: int = BIRTHDAY_DAYS, n: int = BIRTHDAY_YEAR) -> tuple[float, float]:
+    """Mean and variance of the repeat count R of m birthdays in a year of n
+    days (m spacings: the first day and the neighbour differences).
+
+    The m spacings behave as m of the m + 1 exchangeable gaps of m uniform
+    points in [0, n) (Dirichlet(1, ..., 1) scaled by n): two given gaps are
+    equal with probability p = m / (2n) (the density of their difference at
+    0), three with q3 = m (m - 1) / (3 n^2), and two disjoint pairs both
+    equal with m (m - 1) / (4 n^2), slightly less than p^2.  With P2 and P3
+    the numbers of equal pairs and triples, R = P2 - P3 + ... (a value
+    shared by k spacings adds k - 1 = C(k,2) - C(k,3) + ... to R), so
+        E[R]   = C(m,2) p - C(m,3) q3,
+        Var[R] = Var[P2] - 2 Cov[P2, P3] + Var[P3],  Cov[P2, P3] = 3 E[P3],
+    with Var[P2] summed over pairs of pairs: equal, sharing one spacing, or
+    disjoint.  At m = 512, n = 2^24: E[R] = 1.98920, Var[R] = 1.96417, where
+    the Poisson limit m^3 / (4n) = 2 has both equal to 2."""
+    p = m / (2 * n)
+    q3 = m * (m - 1) / (3 * n * n)
+    pairs = math.comb(m, 2)
+    e2 = pairs * p
+    e3 = math.comb(m, 3) * q3
+    var2 = (pairs * p * (1 - p) + m * (m - 1) * (m - 2) * (q3 - p * p)
+            + pairs * math.comb(m - 2, 2) * (m * (m - 1) / (4 * n * n) - p * p))
+    return e2 - e3, var2 - 2 * 3 * e3 + e3
+
+
+def birthday_pmf(kmax: int = 64, m: int = BIRTHDAY_DAYS, n: int = BIRTHDAY_YEAR) -> np.ndarray:
+    """P(R = k), k < kmax: the Poisson law of R's mean with the second-order
+    Charlier term that carries R's variance (the factorial cumulant
+    d = Var[R] - E[R], here -0.025):
+        P(k) = pi(k) + (d / 2) (pi(k) - 2 pi(k - 1) + pi(k - 2)),
+    pi the Poisson(E[R]) probabilities.  (An independent simulation of 2^26
+    samples with numpy's PCG64 fits it: chi-square 7.5 on 7 degrees of
+    freedom; Poisson(2) scores 8825.)"""
+    mu, var = birthday_moments(m, n)
+    d = var - mu
+    pi = np.array([math.exp(-mu) * mu ** k / math.factorial(k) for k in range(kmax)])
+    pi1 = np.concatenate([[0.0], pi[:-1]])
+    pi2 = np.concatenate([[0.0, 0.0], pi[:-2]])
+    return pi + d / 2 * (pi - 2 * pi1 + pi2)
 
 
 def counts(u: torch.Tensor, n_streams: int, n_per_stream: int,
@@ -71,8 +114,8 @@ def statistics(c: dict) -> dict:
     out["serial"] = {"chi2": chi2, "dof": 255, "p": p}
     m = c["birthday_samples"]
     if m:
-        lam = BIRTHDAY_MEAN
-        probs = [math.exp(-lam) * lam ** k / math.factorial(k) for k in range(7)]
+        pmf = birthday_pmf()
+        probs = list(pmf[:7])
         probs.append(1.0 - sum(probs))
         h = c["birthday"].astype(np.float64)
         obs = np.concatenate([h[:7], [h[7:].sum()]])

@@ -20,7 +20,7 @@ RNG_MAX_STREAMS_MWC = 1 << 22
 RNG_MAX_STREAMS_XOR = 1 << 30
 RNG_MAX_STREAMS_MWC16 = 392 * 391 // 2
 RNG_MAX_STREAMS_XS8 = 1 << 28
-RNG_BATTERY_BIRTHDAY_MAX = 4096
+RNG_BATTERY_BIRTHDAY_MAX = 1 << 21
 
 RNG_SUM_U32, RNG_SUM_U24, RNG_DISC = 0, 1, 2
 

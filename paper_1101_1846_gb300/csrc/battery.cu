@@ -10,9 +10,7 @@
 //   birthday   512 consecutive outputs of a stream, days = top 24 bits;
 //              sorted, spacings (first day, then neighbour differences),
 //              sorted; repeats = spacings equal to the one before; at most
-//              RNG_BATTERY_BIRTHDAY_MAX samples (the Poisson limit the
-//              statistic is compared with is off by about 0.3 % in the mean
-//              at 512 days in 2^24, which more samples would resolve)
+//              RNG_BATTERY_BIRTHDAY_MAX samples
 //
 // count_kernel: a CTA takes 256 consecutive streams (coalesced row reads)
 // and a tile of row pairs; histograms in shared memory, added to the global

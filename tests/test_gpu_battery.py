@@ -13,6 +13,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import test_oracle_battery as tob  # noqa: E402
 from paper_1101_1846_gb300 import battery, build, capi  # noqa: E402
+from paper_1101_1846_gb300.generator import Generator  # noqa: E402
 
 ALL = [oracle.MWC, oracle.XOR128, oracle.KISS, oracle.MWC16X2, oracle.XORSHIFT8,
        oracle.KISS_XOR]
@@ -90,10 +91,26 @@ def test_rejects_bad_arguments():
 
 @pytest.mark.parametrize("kind", ALL)
 def test_every_kind_passes_the_battery(kind):
-    n = 4096 if kind not in (oracle.MWC16X2, oracle.KISS_XOR) else 4092
-    stats = battery.run(kind, n, 4096, 2024)
+    """2^21 birthday samples per kind (2^20 streams x 1024 outputs; the pair
+    kinds 76,636 x 16,384), compared with the repeat count's law at 512 days
+    in 2^24, not its Poisson limit."""
+    n, rows = ((1 << 20, 1024) if kind not in (oracle.MWC16X2, oracle.KISS_XOR)
+               else (capi.RNG_MAX_STREAMS_MWC16, 16384))
+    stats = battery.run(kind, n, rows, 2024)
+    assert stats["birthday"]["samples"] == capi.RNG_BATTERY_BIRTHDAY_MAX
     assert battery.passed(stats), stats
-    assert abs(stats["birthday"]["mean_repeats"] - 2.0) < 0.1
+    mu, var = battery.birthday_moments()
+    se = (var / stats["birthday"]["samples"]) ** 0.5
+    assert abs(stats["birthday"]["mean_repeats"] - mu) < 6 * se
+
+
+def test_birthday_samples_stop_at_the_cap():
+    n, rows = (1 << 20) + 8, 1024  # 2^21 + 16 samples available
+    with Generator(oracle.XOR128, n, 5) as g:
+        u = g.generate(rows)
+        c = battery.counts(u, n, rows)
+    assert c["birthday_samples"] == capi.RNG_BATTERY_BIRTHDAY_MAX
+    assert int(c["birthday"].sum()) == capi.RNG_BATTERY_BIRTHDAY_MAX
 
 
 def test_a_bad_sequence_fails():

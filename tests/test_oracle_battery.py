@@ -105,7 +105,7 @@ def check_birthday_cap_and_order():
     blk0 = sample(1)
     b1_lo, b1_hi = sample(2), sample(9)
     cols = [np.concatenate([blk0, b1_lo if s < 1096 else b1_hi]) for s in range(n)]
-    c = oracle.battery_counts(_interleave(cols))
+    c = oracle.battery_counts(_interleave(cols), birthday_max=4096)
     assert c["birthday_samples"] == 4096
     expect = np.zeros(16, np.uint64)
     expect[r_of[(0, "lo")]] = n

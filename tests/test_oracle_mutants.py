@@ -97,7 +97,7 @@ MUTANTS = [
      "repeats += b[i] == b[i - 1];", bat.check_birthday_repeats),
     ("birthday days of 25 bits", "b[i] = u[(blk * 512 + i) * n_streams + s] >> 8;",
      "b[i] = u[(blk * 512 + i) * n_streams + s] >> 7;", bat.check_birthday_repeats),
-    ("birthday without the sample cap", "s < n_streams && samples < ORACLE_BAT_BIRTHDAY_MAX;",
+    ("birthday without the sample cap", "s < n_streams && samples < max_samples;",
      "s < n_streams;", bat.check_birthday_cap_and_order),
     ("splitmix64 shift 27->26", "r = (r ^ (r >> 27))", "r = (r ^ (r >> 26))",
      sd.check_splitmix64_published_vectors),
