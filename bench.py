@@ -630,6 +630,9 @@ def run_ours(args):
             gbs = alg_bytes(k, nn, ss) / (r["ms"] * 1e-3) / 1e9
             summary[name] = {"gsamples_s": round(r["gsamples_s"], 1),
                              "frac": round(gbs / peak, 3)}
+            if nn == 4096:  # 16.8 M samples per call: a latency, not a roofline point
+                summary[name]["us_per_call"] = round(r["ms"] * 1e3, 1)
+                summary[name]["note"] = "latency-bound (few streams, split into jumped segments)"
         if "batched" in line:
             summary["batched_10000"] = {
                 "gsamples_s": round(line["batched"]["value"], 1),
@@ -1088,6 +1091,18 @@ def run_inline(clock_mhz: float):
             "jump_2^22_streams_by_2^40+1_ms": _jump_ms(kind, n, (1 << 40) + 1, 5)}
     probes = run_int_probes(clock_mhz, sms)
     res["int_probes"] = probes
+    # the same rates against the probed peak of each operation class (the
+    # sum consumer's 64-bit add is two adds), as for the writeback kernels
+    for kind in KINDS:
+        kk = res["kinds"][KNAME[kind]]
+        r = int_roofline(kind, 0, kk["sum_u32"]["gsamples_s"] * 1e9, probes)
+        extra = 2 * kk["sum_u32"]["gsamples_s"] * 1e9 / probes["add"]["ops_per_s"]
+        r["classes"]["add"] = r["classes"].get("add", 0.0) + extra
+        r["ops_per_sample"]["add"] = r["ops_per_sample"].get("add", 0) + 2
+        r["bound"] = max(r["classes"], key=r["classes"].get)
+        r["frac"] = r["classes"][r["bound"]]
+        r["serial"] = sum(r["classes"].values())
+        kk["int_probe_roofline"] = r
     mwc = res["kinds"]["mwc"]["sum_u32"]["gsamples_s"] * 1e9
     res["kinds"]["mwc"]["of_probed_mwc_step_rate"] = mwc / probes["mwc_step"]["ops_per_s"]
     # few streams: the 4096 x 4096 MWC call with and without splitting
