@@ -914,7 +914,7 @@ def _flush_l2(_buf=[]):
     _buf[0].fill_(0)
 
 
-def _plain_rate(kind, n, steps, fmt, seed, reps=5):
+def _plain_rate(kind, n, steps, fmt, seed, reps=11):
     """Median CUDA-event time of one rng_generate call (the L2 is flushed
     before each timed call whose output is smaller than four L2s)."""
     import torch

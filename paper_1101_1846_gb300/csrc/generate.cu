@@ -23,14 +23,16 @@ struct Shape {
 // staging its own rows, no block barrier) were slower than both.
 //
 // Two size classes: calls of fewer than kSmallStreams streams (class 0) and
-// the rest (class 1).  At 2^20 streams x 1024 the FP32 forms fill the GPU
-// differently: xor128 FP32 ran 1345 GS/s with its 2^22 shape (1, 128) and
-// 1608 with (2, 128); KISS FP32 1580 with (2, 512) and 1789 with (1, 256).
+// the rest (class 1).  At 2^20 streams x 1024 the kernels fill the GPU
+// differently (medians of three sweeps of every shape on one GB300): xor128
+// FP32 ran 1345 GS/s with its 2^22 shape (1, 128) and 1615 with (2, 128);
+// KISS FP32 1580 with (2, 512), 1619 with (1, 256) and 1706 with (1, 128);
+// xor128 uint32 1691 through TMA and 1728 with (1, 128) and plain stores.
 Shape g_shape[2][kKinds][2] = {
     {
         {{1, 256, 2}, {2, 512, 1}},  // MWC u32, f32
-        {{1, 256, 2}, {2, 128, 1}},  // xor128
-        {{2, 512, 1}, {1, 256, 1}},  // KISS
+        {{1, 128, 0}, {2, 128, 1}},  // xor128
+        {{2, 512, 1}, {1, 128, 1}},  // KISS
         {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
         {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
         {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
