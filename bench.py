@@ -637,6 +637,8 @@ def run_ours(args):
             summary["batched_10000"] = {
                 "gsamples_s": round(line["batched"]["value"], 1),
                 "over_plain_full_device": round(line["batched"]["over_plain_full_device"], 3)}
+            if "roofline" in line["batched"]:
+                summary["batched_10000"]["frac"] = round(line["batched"]["roofline"]["frac"], 3)
         if sat:
             summary["serving_saturating"] = {
                 "gsamples_s": round(sat["gsamples_s"], 1),
@@ -709,6 +711,10 @@ def run_batched(args):
     tiles = run.tiles
 
     samples = sum(i.n_streams * i.n_per_stream for i in inst)
+    # bytes the waves must move: every piece writes its rows and reads and
+    # writes back its streams' state (and reads their multipliers)
+    moved = sum(alg_bytes(inst[p.inst].kind, inst[p.inst].n_streams, p.rows)
+                for w in waves for p in w)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(main)
     run.replay()
@@ -765,6 +771,10 @@ def run_batched(args):
         "bit_identical": (mismatched == 0 and states_equal) if not args.no_verify else None,
         "pieces_checked": checked, "mismatched_pieces": mismatched, "create_s": create_s,
         "realigned_instances": sum(1 for i in inst if i.n_streams % 4),
+        "roofline": {"bound": "hbm", "algorithmic_bytes": moved,
+                     "state_bytes_over_output": moved / (4 * samples) - 1,
+                     "achieved": moved / (b_ms * 1e-3) / 1e9, "peak": peaks()[0],
+                     "frac": moved / (b_ms * 1e-3) / 1e9 / peaks()[0], "unit": "GB/s"},
         "config": {"workload": "batched", "instances": args.instances, "seed": 1234,
                    "wave_bytes": budget, "graph": "one CUDA graph per wave",
                    "order": f"{lanes} lanes: a lane's waves in order on its own stream "
@@ -1187,7 +1197,7 @@ def run_extras(args, clock_mhz: float = 2070.0):
     extras["battery"] = run_battery()
     keep = ("value", "plain_per_instance_value", "bit_identical", "pieces_checked",
             "mismatched_pieces", "waves", "pieces", "tiles", "chunk_rows", "plan_shape",
-            "batched_ms", "gpu_launches")
+            "batched_ms", "gpu_launches", "roofline")
     b = run_batched(args)  # the library's default plan shape (--tune to sweep shapes)
     extras["batched"] = {k: b[k] for k in keep if k in b}
     s = run_serving(args)
