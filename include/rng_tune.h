@@ -31,6 +31,14 @@ int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
 int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, int block, int hint);
 int gbrng_get_launch_class(int kind, int fmt, int size_class, int *v, int *block, int *hint);
 
+/* CTAs per SM of the kernels for rows that are 16- but not 32-byte aligned
+ * (realigned = 0) and for rows that are not 16-byte aligned (realigned = 1),
+ * per (kind, fmt): 1 = one CTA of 512 threads per SM (a shared-memory
+ * reservation keeps a second one off the SM), 0 = as many as fit.  Outputs
+ * never change.  Returns 0 or RNG_ERR_ARG. */
+int gbrng_set_row_ctas(int kind, int fmt, int realigned, int ctas_per_sm);
+int gbrng_get_row_ctas(int kind, int fmt, int realigned, int *ctas_per_sm);
+
 /* Sequence splitting of few-stream calls (rng_generate, rng_generate_reduce):
  * `log2_rows` is log2 of the fewest rows a segment may have for `kind`
  * (1..30); 0 turns splitting off for the kind.  A split generate call takes

@@ -189,21 +189,25 @@ batch_kernel_mixed(const Unit *__restrict__ units, uint64_t n_units, unsigned lo
     }
 }
 
-// Launches the mapped-tile kernel of `kind`.
-void launch_mixed(int kind, int grid, int threads, cudaStream_t st, const Unit *units,
-                  uint64_t n_units, unsigned long long *next)
+// Launches the mapped-tile kernel of `kind`; one_per_sm: reserve the shared
+// memory that keeps the grid to one CTA per SM.
+void launch_mixed(int kind, int grid, int threads, bool one_per_sm, cudaStream_t st,
+                  const Unit *units, uint64_t n_units, unsigned long long *next)
 {
-    if (kind == RNG_MWC32)
-        batch_kernel_mixed<RNG_MWC32, 1><<<grid, threads, 0, st>>>(units, n_units, next);
-    else if (kind == RNG_XOR128)
-        batch_kernel_mixed<RNG_XOR128, 1><<<grid, threads, 0, st>>>(units, n_units, next);
-    else
-        batch_kernel_mixed<RNG_KISS, 1><<<grid, threads, 0, st>>>(units, n_units, next);
+    auto fn = kind == RNG_MWC32    ? batch_kernel_mixed<RNG_MWC32, 1>
+              : kind == RNG_XOR128 ? batch_kernel_mixed<RNG_XOR128, 1>
+                                   : batch_kernel_mixed<RNG_KISS, 1>;
+    const int smem = one_per_sm ? one_cta_smem((const void *)fn, threads) : 0;
+    fn<<<grid, threads, smem, st>>>(units, n_units, next);
 }
 
-// CTA size when the caller passes 0: 512 was the fastest on GB300 for the
-// 10,000-instance workload (914 GSamples/s at 128, about 1570 at 512).
+// Plan shape when the caller passes 0 for both: CTAs of 512 threads, one per
+// SM.  Measured on GB300 with the 10,000-instance workload: 914 GSamples/s
+// with 128 threads (as many CTAs as fit), about 1570 with 512 (two per SM);
+// then, on one box, 1605 with two CTAs of 512 per SM, 1632 with one, 1504
+// with two of 256.  Serving, saturating: 1631 with two, 1641 with one.
 constexpr int kDefaultThreads = 512;
+constexpr int kDefaultCtas = 1;
 constexpr int kHint = 1;  // streaming stores, as the plain kernels
 
 // An item's stream range and row stride with the defaults filled in.
@@ -405,6 +409,8 @@ extern "C" rng_plan_handle rng_plan_create(const rng_batch_item *items, size_t n
         set_error(RNG_ERR_ARG);
         return nullptr;
     }
+    if (threads == 0 && ctas_per_sm == 0)
+        ctas_per_sm = kDefaultCtas;
     if (threads == 0)
         threads = kDefaultThreads;
     if (threads < 32 || threads > 512 || (threads & (threads - 1)) || ctas_per_sm < 0 ||
@@ -466,12 +472,16 @@ extern "C" int rng_plan_launch(rng_plan_handle h, void *cuda_stream)
         cudaSetDevice(p->device);
     int status = cuda_status(cudaMemsetAsync(p->d_next, 0, sizeof(unsigned long long), st));
     if (!status) {
-        if (p->mixed)
-            launch_mixed(p->mixed_kind, p->grid_mixed, p->threads, st, p->d_units, p->n_units,
-                         p->d_next);
-        else
-            batch_kernel<kHint><<<p->grid, p->threads, 0, st>>>(p->d_units, p->n_units,
-                                                               p->d_next);
+        const bool one = p->ctas_per_sm == 1;
+        if (p->mixed) {
+            launch_mixed(p->mixed_kind, p->grid_mixed, p->threads, one, st, p->d_units,
+                         p->n_units, p->d_next);
+        } else {
+            const int smem = one ? one_cta_smem((const void *)batch_kernel<kHint>, p->threads)
+                                 : 0;
+            batch_kernel<kHint><<<p->grid, p->threads, smem, st>>>(p->d_units, p->n_units,
+                                                                  p->d_next);
+        }
         status = cuda_status(cudaGetLastError());
     }
     if (prev >= 0 && prev != p->device)

@@ -77,6 +77,14 @@ struct LaunchShape {
 };
 // The shape for a call of `streams` streams (its size class).
 LaunchShape launch_shape(int kind, int fmt, uint64_t streams);
+// CTAs per SM of the barrier-synced kernels for rows that are not 32-byte
+// aligned (realigned: rows not 16-byte aligned): 1, or 0 for as many as fit.
+int row_ctas(int kind, int fmt, bool realigned);
+// Dynamic shared memory that keeps `kernel`, launched with `threads`
+// threads, to one CTA per SM: more than half an SM's shared memory (nothing
+// is stored there; the reservation only bars a second CTA).  0 when the
+// device cannot tell or the kernel would not fit; sets the kernel's limit.
+int one_cta_smem(const void *kernel, int threads);
 int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st);
 // generate_paper.cu: the same for RNG_MWC16X2, RNG_XORSHIFT8, RNG_KISS_XOR.
 int launch_generate_paper(int kind, int fmt, const GenLaunch &p, cudaStream_t st);

@@ -395,8 +395,11 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
             uint64_t blocks = (count / 4 + threads - 1) / threads;
             if (blocks > 0x7FFFFFFFull)
                 return set_error(RNG_ERR_ARG);
-            sync<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
-                                                       p.s_begin, count);
+            const int smem = row_ctas(KIND, fmt, false) && threads == kSyncBlock
+                                 ? one_cta_smem((const void *)sync, threads)
+                                 : 0;
+            sync<<<(unsigned)blocks, threads, smem, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                          p.s_begin, count);
         } else if (aligned && sh.hint == 2) {
             // outputs staged in shared memory, rows written by bulk copies
             const uint64_t blocks = (count + 4 * kTmaThreads - 1) / (4 * kTmaThreads);
@@ -424,8 +427,11 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
             uint64_t blocks = (main / 4 + per_cta - 1) / per_cta + (count > main ? 1 : 0);
             if (blocks > 0x7FFFFFFFull)
                 return set_error(RNG_ERR_ARG);
-            shift<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
-                                                        p.s_begin, count);
+            const int smem = row_ctas(KIND, fmt, true) && threads == kSyncBlock
+                                 ? one_cta_smem((const void *)shift, threads)
+                                 : 0;
+            shift<<<(unsigned)blocks, threads, smem, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                           p.s_begin, count);
         }
         int e = cuda_status(cudaGetLastError());
         if (e)

@@ -2,6 +2,9 @@
 // dispatch of a call to its kind's launcher (gen_kernels.cuh): the three
 // target kinds are instantiated here, the paper's own generators in
 // generate_paper.cu.
+#include <mutex>
+#include <vector>
+
 #include "gen_kernels.cuh"
 #include "rng_tune.h"
 
@@ -48,6 +51,25 @@ Shape g_shape[2][kKinds][2] = {
 };
 constexpr uint64_t kSmallStreams = (uint64_t)1 << 21;
 
+// CTAs per SM of the barrier-synced kernels, [kind][fmt][realigned]: 1 =
+// one CTA of 512 threads per SM, 0 = as many as fit (two at their register
+// counts).  Measured on GB300 at (2^22 - 4) x 1024 (16-byte rows) and
+// (2^22 - 2) x 1024 (realigned), GS/s with two CTAs -> with one:
+//   MWC u32 1760 -> 1766 / 1686 -> 1756;  MWC f32 1717 -> 1783 / 1694 -> 1772
+//   xor128 u32 1663 -> 1746 / 1689 -> 1753;  xor128 f32 1670 -> 1695 / 1710 -> 1685
+//   KISS u32 1713 -> 1797 / 1683 -> 1744;  KISS f32 1720 -> 1617 / 1690 -> 1441
+// Where the step is cheap, fewer warps writing at once keep the write
+// stream denser; the FP32 forms of xor128 and KISS need the second CTA's
+// warps to cover their arithmetic.  The paper's kinds keep 0 (not measured).
+int g_row_ctas[kKinds][2][2] = {
+    {{1, 1}, {1, 1}},  // MWC u32 (16-byte rows, realigned), f32
+    {{1, 1}, {1, 0}},  // xor128
+    {{1, 1}, {0, 0}},  // KISS
+    {{0, 0}, {0, 0}},  // MWC16X2
+    {{0, 0}, {0, 0}},  // XORSHIFT8
+    {{0, 0}, {0, 0}},  // KISS_XOR
+};
+
 // Fewest rows of a split segment, as log2, per kind (0: never split).  The
 // jump that starts a segment costs about as much as this many rows: MWC32 a
 // tabulated Montgomery product, KISS that plus 32-column GF(2) products,
@@ -71,6 +93,62 @@ LaunchShape launch_shape(int kind, int fmt, uint64_t streams)
 {
     const Shape s = g_shape[streams < kSmallStreams ? 0 : 1][kind][fmt];
     return LaunchShape{s.v, s.block, s.hint};
+}
+
+int row_ctas(int kind, int fmt, bool realigned)
+{
+    return g_row_ctas[kind][fmt][realigned ? 1 : 0];
+}
+
+namespace {
+
+// The smallest multiple of 1 KB of dynamic shared memory above half an SM's
+// share (less the per-CTA reservation), if the kernel then fits one CTA.
+int find_one_cta_smem(const void *kernel, int threads, int dev)
+{
+    int per_sm = 0, reserved = 0, optin = 0, fit = 0;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+        return 0;
+    // two CTAs would need 2 * (smem + reserved) > per_sm
+    const int smem = ((per_sm / 2 - reserved + 1 + 1023) / 1024) * 1024;
+    if (smem <= 0 || smem > optin ||
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, smem) !=
+            cudaSuccess ||
+        fit != 1) {
+        cudaGetLastError();  // leave no sticky error from the probe behind
+        return 0;
+    }
+    return smem;
+}
+
+}  // namespace
+
+int one_cta_smem(const void *kernel, int threads)
+{
+    // answers per (kernel, threads, device), found once each
+    struct Known {
+        const void *kernel;
+        int threads, dev, smem;
+    };
+    static std::mutex mu;
+    static std::vector<Known> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Known &k : known)
+        if (k.kernel == kernel && k.threads == threads && k.dev == dev)
+            return k.smem;
+    const int smem = find_one_cta_smem(kernel, threads, dev);
+    known.push_back(Known{kernel, threads, dev, smem});
+    return smem;
 }
 
 uint64_t split_fill(bool reduce)
@@ -119,6 +197,26 @@ int launch_generate(int kind, int fmt, const GenLaunch &p, cudaStream_t st)
 }
 
 }  // namespace gbrng
+
+extern "C" int gbrng_set_row_ctas(int kind, int fmt, int realigned, int ctas_per_sm)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || realigned < 0 || realigned > 1 ||
+        ctas_per_sm < 0 || ctas_per_sm > 1)
+        return set_error(RNG_ERR_ARG);
+    g_row_ctas[kind][fmt][realigned] = ctas_per_sm;
+    return RNG_OK;
+}
+
+extern "C" int gbrng_get_row_ctas(int kind, int fmt, int realigned, int *ctas_per_sm)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || realigned < 0 || realigned > 1 ||
+        !ctas_per_sm)
+        return set_error(RNG_ERR_ARG);
+    *ctas_per_sm = g_row_ctas[kind][fmt][realigned];
+    return RNG_OK;
+}
 
 extern "C" int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, int block,
                                       int hint)

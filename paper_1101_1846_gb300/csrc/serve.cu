@@ -36,6 +36,7 @@ constexpr uint64_t kGranule = 256;  // arena alignment, bytes
 constexpr int kMaxInflight = 2;     // ticks in flight per lane
 constexpr int kLanes = 2;           // client c belongs to lane c % kLanes
 constexpr int kServeThreads = 512;
+constexpr int kServeCtas = 1;  // one CTA per SM: 1641 against 1631 GS/s (two) saturating
 
 // Arena bytes of a request of n samples: its output and room to place it at
 // the word phase of its first sample (placement_pad).
@@ -110,7 +111,7 @@ struct Server {
     cudaEvent_t t0 = nullptr;
     uint32_t rr[kLanes] = {};  // round-robin start, per lane
     uint64_t tick_bytes = 0;  // target output per tick (0: chunk_rows alone)
-    int plan_threads = kServeThreads, plan_ctas = 0;  // persistent kernel shape
+    int plan_threads = kServeThreads, plan_ctas = kServeCtas;  // persistent kernel shape
     uint64_t next_id = 0, n_admitted = 0, n_completed = 0, n_ticks = 0, samples = 0;
 };
 

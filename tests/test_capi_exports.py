@@ -129,3 +129,19 @@ def test_missing_library_fails_loudly(tmp_path):
     ) % (str(ROOT), str(tmp_path / "absent" / "libgbrng.so"))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.stdout.strip() == "raised True", r.stdout + r.stderr[-2000:]
+
+
+def test_row_ctas_roundtrip(lib):
+    """The CTAs-per-SM choice of the barrier-synced kernels, per (kind, fmt,
+    realigned): 0 or 1, anything else rejected; defaults one CTA for the
+    memory-bound forms, as many as fit for KISS FP32."""
+    v = ctypes.c_int()
+    assert lib.gbrng_get_row_ctas(2, 1, 1, ctypes.byref(v)) == 0 and v.value == 0
+    assert lib.gbrng_get_row_ctas(0, 0, 1, ctypes.byref(v)) == 0 and v.value == 1
+    assert lib.gbrng_set_row_ctas(0, 0, 1, 0) == 0
+    lib.gbrng_get_row_ctas(0, 0, 1, ctypes.byref(v))
+    assert v.value == 0
+    assert lib.gbrng_set_row_ctas(0, 0, 1, 1) == 0
+    for bad in [(6, 0, 0, 1), (0, 2, 0, 1), (0, 0, 2, 1), (0, 0, 0, 2), (0, 0, 0, -1)]:
+        assert lib.gbrng_set_row_ctas(*bad) == capi.RNG_ERR_ARG
+    assert lib.gbrng_get_row_ctas(0, 0, 0, None) == capi.RNG_ERR_ARG

@@ -223,6 +223,33 @@ def test_launch_shapes_do_not_change_outputs():
         capi.check(L.gbrng_set_launch_class(k, oracle.F32, 0, *saved[k]))
 
 
+def test_row_ctas_do_not_change_outputs():
+    """The barrier-synced kernels (16-byte rows: n % 8 == 4; realigned rows:
+    odd n) with one CTA of 512 threads per SM (a shared-memory reservation)
+    and with as many as fit, at sizes that fill the GPU: the two outputs are
+    identical, and sampled streams equal the oracle."""
+    L = capi.lib()
+    steps, seed = 8, 5
+    for n, realigned in (((1 << 20) + 4, 0), ((1 << 20) + 3, 1)):
+        for k in KINDS:
+            idx = np.array(sorted(i for i in golden_streams(n).tolist() if i < (1 << 20)))
+            a = golden_a(idx) if k != oracle.XOR128 else None
+            st = oracle.seed_streams(k, a, seed, idx)
+            for f in FMTS:
+                exp, _ = oracle.generate(k, a, st, steps, f)
+                v = ctypes.c_int()
+                capi.check(L.gbrng_get_row_ctas(k, f, realigned, ctypes.byref(v)))
+                outs = []
+                for ctas in (0, 1):
+                    capi.check(L.gbrng_set_row_ctas(k, f, realigned, ctas))
+                    outs.append(Generator(k, n, seed).generate(steps, f))
+                    torch.cuda.synchronize()
+                capi.check(L.gbrng_set_row_ctas(k, f, realigned, v.value))
+                assert torch.equal(outs[0].view(torch.int32), outs[1].view(torch.int32)), (n, k, f)
+                got = bits(outs[1].index_select(1, torch.as_tensor(idx, device="cuda")))
+                assert np.array_equal(got, obits(exp)), (n, k, f)
+
+
 # --------------------------------------------------------- the workloads
 @pytest.mark.parametrize("fmt", FMTS)
 def test_mwc_4096x4096_full(fmt):
