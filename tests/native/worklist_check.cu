@@ -15,6 +15,7 @@
 namespace gbrng {
 int set_error(int status) { return status; }
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? 0 : RNG_ERR_CUDA; }
+int one_cta_smem(const void *, int) { return 0; }
 }  // namespace gbrng
 extern "C" int rng_last_error(void) { return 0; }
 
