@@ -31,6 +31,14 @@ int gbrng_get_launch(int kind, int fmt, int *v, int *block, int *hint);
 int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, int block, int hint);
 int gbrng_get_launch_class(int kind, int fmt, int size_class, int *v, int *block, int *hint);
 
+/* One CTA per SM (1) or as many as fit (0) for the aligned vector kernel of
+ * (kind, fmt) in a size class (as gbrng_set_launch_class): with 1, a
+ * shared-memory reservation keeps a second CTA off each SM whenever the
+ * call runs CTAs of the shape's size.  gbrng_set_launch(_class) leave it
+ * as it is.  Outputs never change.  Returns 0 or RNG_ERR_ARG. */
+int gbrng_set_launch_ctas(int kind, int fmt, int size_class, int ctas_per_sm);
+int gbrng_get_launch_ctas(int kind, int fmt, int size_class, int *ctas_per_sm);
+
 /* CTAs per SM of the kernels for rows that are 16- but not 32-byte aligned
  * (realigned = 0) and for rows that are not 16-byte aligned (realigned = 1),
  * per (kind, fmt): 1 = one CTA of 512 threads per SM (a shared-memory

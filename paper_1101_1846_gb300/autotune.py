@@ -1,8 +1,10 @@
 """Launch-shape autotuner.
 
 Plain kernels: for each (kind, fmt), time the vector kernel under each
-candidate shape (groups of four streams per thread V, CTA size, store hint)
-on a caller-given problem and keep the fastest through gbrng_set_launch.
+candidate shape (groups of four streams per thread V, CTA size, store hint,
+one CTA per SM or as many as fit) on a caller-given problem and keep the
+fastest through gbrng_set_launch and gbrng_set_launch_ctas (the shapes of
+calls of 2^21 streams or more).
 Batched plans: time a plan under candidate (CTA size, CTAs per SM) pairs and
 return the fastest.  Shapes never change outputs (tests check this), only
 speed.  Results can be saved to and loaded from a JSON file keyed by GPU.
@@ -18,7 +20,8 @@ import torch
 from . import capi
 from .generator import BatchItem, Generator, Plan
 
-PLAIN_CANDIDATES = [(v, b, h) for v in (1, 2) for b in (128, 256, 512) for h in (0, 1)]
+PLAIN_CANDIDATES = ([(v, b, h, 0) for v in (1, 2) for b in (128, 256, 512) for h in (0, 1)] +
+                    [(v, 512, h, 1) for v in (1, 2) for h in (0, 1)])
 PLAN_CANDIDATES = [(64, 0), (128, 0), (256, 0), (512, 0), (128, 4), (256, 2)]
 
 
@@ -39,15 +42,22 @@ def _time(fn, reps: int, stream) -> float:
     return times[len(times) // 2]
 
 
-def get_shape(kind: int, fmt: int) -> tuple[int, int, int]:
-    v, b, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    capi.check(capi.lib().gbrng_get_launch(kind, fmt, ctypes.byref(v), ctypes.byref(b),
-                                           ctypes.byref(h)))
-    return v.value, b.value, h.value
+def get_shape(kind: int, fmt: int) -> tuple[int, int, int, int]:
+    """(V, CTA size, store hint, one CTA per SM) of calls of 2^21 streams or more."""
+    v, b, h, one = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib = capi.lib()
+    capi.check(lib.gbrng_get_launch(kind, fmt, ctypes.byref(v), ctypes.byref(b),
+                                    ctypes.byref(h)))
+    capi.check(lib.gbrng_get_launch_ctas(kind, fmt, 1, ctypes.byref(one)))
+    return v.value, b.value, h.value, one.value
 
 
 def set_shape(kind: int, fmt: int, shape) -> None:
-    capi.check(capi.lib().gbrng_set_launch(kind, fmt, *shape), "gbrng_set_launch")
+    """shape: (V, CTA size, store hint[, one CTA per SM])."""
+    lib = capi.lib()
+    capi.check(lib.gbrng_set_launch(kind, fmt, *shape[:3]), "gbrng_set_launch")
+    if len(shape) > 3:
+        capi.check(lib.gbrng_set_launch_ctas(kind, fmt, 1, shape[3]), "gbrng_set_launch_ctas")
 
 
 def tune_plain(n_streams: int = 1 << 22, n_per_stream: int = 256, kinds=(0, 1, 2),

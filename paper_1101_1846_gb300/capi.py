@@ -121,6 +121,8 @@ SIGNATURES = {
                                [ctypes.POINTER(ctypes.c_int)] * 3),
     "gbrng_get_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] +
                          [ctypes.POINTER(ctypes.c_int)] * 3),
+    "gbrng_set_launch_ctas": (ctypes.c_int, [ctypes.c_int] * 4),
+    "gbrng_get_launch_ctas": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)]),
     "gbrng_set_row_ctas": (ctypes.c_int, [ctypes.c_int] * 4),
     "gbrng_get_row_ctas": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int)]),
     "gbrng_set_split": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),

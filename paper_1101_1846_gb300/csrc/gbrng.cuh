@@ -74,6 +74,7 @@ struct LaunchShape {
     int v;      // groups of four streams per thread
     int block;  // CTA size
     int hint;   // streaming stores
+    int one;    // one CTA per SM
 };
 // The shape for a call of `streams` streams (its size class).
 LaunchShape launch_shape(int kind, int fmt, uint64_t streams);

@@ -418,8 +418,12 @@ int launch_kind(int fmt, const GenLaunch &p, cudaStream_t st)
             uint64_t blocks = (groups + per_block - 1) / per_block;
             if (blocks > 0x7FFFFFFFull)
                 return set_error(RNG_ERR_ARG);
-            vec<<<(unsigned)blocks, threads, 0, st>>>(p.state, p.a, p.n, steps, o, p.ld,
-                                                      p.s_begin, count);
+            // one CTA per SM only for the shape's own CTA size (small calls
+            // halve it above to fill the SMs)
+            const int smem =
+                sh.one && threads == sh.block ? one_cta_smem((const void *)vec, threads) : 0;
+            vec<<<(unsigned)blocks, threads, smem, st>>>(p.state, p.a, p.n, steps, o, p.ld,
+                                                         p.s_begin, count);
         } else {
             // realigned groups plus, when count % 4 != 0, one more CTA for the tail
             int threads = fit_threads(kSyncBlock, main / 4);

@@ -12,12 +12,15 @@ namespace gbrng {
 namespace {
 
 // Launch shape per (kind, fmt): groups of four streams per thread V, CTA
-// size, store hint.  Defaults are the best measured on GB300 at 2^22 streams
-// x 1024 outputs; gbrng_set_launch changes them (the autotuner does).
+// size, store hint, and one = one CTA per SM (a shared-memory reservation
+// keeps a second CTA off the SM).  Defaults are the best measured on GB300;
+// gbrng_set_launch / gbrng_set_launch_class change the first three (the
+// autotuner does), gbrng_set_launch_ctas the last.
 struct Shape {
     int v;
     int block;
     int hint;
+    int one;
 };
 // MWC and xor128 uint32 write their rows through TMA bulk copies (hint 2):
 // 6 % and 1.4 % faster per launch on GB300 than 16-byte stores; the FP32
@@ -31,22 +34,30 @@ struct Shape {
 // FP32 ran 1345 GS/s with its 2^22 shape (1, 128) and 1615 with (2, 128);
 // KISS FP32 1580 with (2, 512), 1619 with (1, 256) and 1706 with (1, 128);
 // xor128 uint32 1691 through TMA and 1728 with (1, 128) and plain stores.
+//
+// One CTA of 512 threads per SM, against the best shapes without it (two
+// rounds on one GB300, GS/s): at 2^22 x 1024, MWC f32 1807 -> 1821, xor128
+// u32 1790-1800 (TMA) -> 1804, xor128 f32 1771 -> 1805, KISS u32 1757 ->
+// 1797, KISS f32 1716 -> 1813 (with plain stores; 1765 streaming); MWC u32
+// stays with TMA (1823 against 1818).  At 2^20 x 1024 only xor128 f32 gains
+// (1609-1614 -> 1717 with V = 2).  As for the barrier-synced kernels, fewer
+// warps writing at once keep each SM's write stream denser.
 Shape g_shape[2][kKinds][2] = {
     {
-        {{1, 256, 2}, {2, 512, 1}},  // MWC u32, f32
-        {{1, 128, 0}, {2, 128, 1}},  // xor128
-        {{2, 512, 1}, {1, 128, 1}},  // KISS
-        {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
-        {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
-        {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
+        {{1, 256, 2, 0}, {2, 512, 1, 0}},  // MWC u32, f32
+        {{1, 128, 0, 0}, {2, 512, 1, 1}},  // xor128
+        {{2, 512, 1, 0}, {1, 128, 1, 0}},  // KISS
+        {{2, 256, 1, 0}, {2, 256, 1, 0}},  // MWC16X2
+        {{1, 256, 1, 0}, {1, 256, 1, 0}},  // XORSHIFT8 (eight state words per stream)
+        {{2, 256, 1, 0}, {2, 256, 1, 0}},  // KISS_XOR
     },
     {
-        {{1, 256, 2}, {2, 256, 1}},  // MWC u32, f32
-        {{1, 256, 2}, {1, 128, 1}},  // xor128
-        {{2, 512, 1}, {2, 512, 1}},  // KISS
-        {{2, 256, 1}, {2, 256, 1}},  // MWC16X2
-        {{1, 256, 1}, {1, 256, 1}},  // XORSHIFT8 (eight state words per stream)
-        {{2, 256, 1}, {2, 256, 1}},  // KISS_XOR
+        {{1, 256, 2, 0}, {1, 512, 1, 1}},  // MWC u32, f32
+        {{1, 512, 1, 1}, {1, 512, 1, 1}},  // xor128
+        {{1, 512, 1, 1}, {1, 512, 0, 1}},  // KISS
+        {{2, 256, 1, 0}, {2, 256, 1, 0}},  // MWC16X2
+        {{1, 256, 1, 0}, {1, 256, 1, 0}},  // XORSHIFT8 (eight state words per stream)
+        {{2, 256, 1, 0}, {2, 256, 1, 0}},  // KISS_XOR
     },
 };
 constexpr uint64_t kSmallStreams = (uint64_t)1 << 21;
@@ -92,7 +103,7 @@ constexpr uint64_t kSplitFillThreads = (uint64_t)kSMs * 2048;
 LaunchShape launch_shape(int kind, int fmt, uint64_t streams)
 {
     const Shape s = g_shape[streams < kSmallStreams ? 0 : 1][kind][fmt];
-    return LaunchShape{s.v, s.block, s.hint};
+    return LaunchShape{s.v, s.block, s.hint, s.one};
 }
 
 int row_ctas(int kind, int fmt, bool realigned)
@@ -226,7 +237,30 @@ extern "C" int gbrng_set_launch_class(int kind, int fmt, int size_class, int v, 
         (v != 1 && v != 2) || block < 32 || block > 512 || (block & (block - 1)) || hint < 0 ||
         hint > 2)
         return set_error(RNG_ERR_ARG);
-    g_shape[size_class][kind][fmt] = Shape{v, block, hint};
+    Shape &s = g_shape[size_class][kind][fmt];
+    s.v = v;
+    s.block = block;
+    s.hint = hint;
+    return RNG_OK;
+}
+
+extern "C" int gbrng_set_launch_ctas(int kind, int fmt, int size_class, int ctas_per_sm)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || size_class < 0 || size_class > 1 ||
+        ctas_per_sm < 0 || ctas_per_sm > 1)
+        return set_error(RNG_ERR_ARG);
+    g_shape[size_class][kind][fmt].one = ctas_per_sm;
+    return RNG_OK;
+}
+
+extern "C" int gbrng_get_launch_ctas(int kind, int fmt, int size_class, int *ctas_per_sm)
+{
+    using namespace gbrng;
+    if (kind < 0 || kind >= kKinds || fmt < 0 || fmt > 1 || size_class < 0 || size_class > 1 ||
+        !ctas_per_sm)
+        return set_error(RNG_ERR_ARG);
+    *ctas_per_sm = g_shape[size_class][kind][fmt].one;
     return RNG_OK;
 }
 

@@ -145,3 +145,24 @@ def test_row_ctas_roundtrip(lib):
     for bad in [(6, 0, 0, 1), (0, 2, 0, 1), (0, 0, 2, 1), (0, 0, 0, 2), (0, 0, 0, -1)]:
         assert lib.gbrng_set_row_ctas(*bad) == capi.RNG_ERR_ARG
     assert lib.gbrng_get_row_ctas(0, 0, 0, None) == capi.RNG_ERR_ARG
+
+
+def test_launch_ctas_roundtrip(lib):
+    """One CTA per SM for the aligned vector kernel, per (kind, fmt, size
+    class): kept when the shape itself is set, 0 or 1 only."""
+    v, b, h, one = (ctypes.c_int() for _ in range(4))
+    assert lib.gbrng_get_launch_ctas(2, 1, 1, ctypes.byref(one)) == 0 and one.value == 1
+    assert lib.gbrng_get_launch_ctas(2, 1, 0, ctypes.byref(one)) == 0 and one.value == 0
+    lib.gbrng_get_launch_class(2, 1, 1, ctypes.byref(v), ctypes.byref(b), ctypes.byref(h))
+    old = (v.value, b.value, h.value)
+    assert lib.gbrng_set_launch_class(2, 1, 1, 2, 256, 1) == 0
+    lib.gbrng_get_launch_ctas(2, 1, 1, ctypes.byref(one))
+    assert one.value == 1
+    assert lib.gbrng_set_launch_ctas(2, 1, 1, 0) == 0
+    lib.gbrng_get_launch_ctas(2, 1, 1, ctypes.byref(one))
+    assert one.value == 0
+    assert lib.gbrng_set_launch_ctas(2, 1, 1, 1) == 0
+    assert lib.gbrng_set_launch_class(2, 1, 1, *old) == 0
+    for bad in [(6, 0, 0, 1), (0, 2, 0, 1), (0, 0, 2, 1), (0, 0, 0, 2)]:
+        assert lib.gbrng_set_launch_ctas(*bad) == capi.RNG_ERR_ARG
+    assert lib.gbrng_get_launch_ctas(0, 0, 0, None) == capi.RNG_ERR_ARG

@@ -250,6 +250,36 @@ def test_row_ctas_do_not_change_outputs():
                 assert np.array_equal(got, obits(exp)), (n, k, f)
 
 
+def test_launch_ctas_do_not_change_outputs():
+    """The aligned vector kernel with one CTA per SM and with as many as fit,
+    at 2^21 streams (the size class of the full-device calls): identical
+    outputs, and sampled streams equal to the oracle."""
+    L = capi.lib()
+    n, steps, seed = 1 << 21, 4, 9
+    idx = golden_streams(n)
+    for k in KINDS:
+        a = golden_a(idx) if k != oracle.XOR128 else None
+        st = oracle.seed_streams(k, a, seed, idx)
+        for f in FMTS:
+            exp, _ = oracle.generate(k, a, st, steps, f)
+            v, b, h, one = (ctypes.c_int() for _ in range(4))
+            capi.check(L.gbrng_get_launch_class(k, f, 1, ctypes.byref(v), ctypes.byref(b),
+                                                ctypes.byref(h)))
+            capi.check(L.gbrng_get_launch_ctas(k, f, 1, ctypes.byref(one)))
+            outs = []
+            for shape, ctas in (((1, 512, 1), 0), ((1, 512, 1), 1), ((2, 512, 0), 1)):
+                capi.check(L.gbrng_set_launch_class(k, f, 1, *shape))
+                capi.check(L.gbrng_set_launch_ctas(k, f, 1, ctas))
+                outs.append(Generator(k, n, seed).generate(steps, f))
+                torch.cuda.synchronize()
+            capi.check(L.gbrng_set_launch_class(k, f, 1, v.value, b.value, h.value))
+            capi.check(L.gbrng_set_launch_ctas(k, f, 1, one.value))
+            for o in outs[1:]:
+                assert torch.equal(outs[0].view(torch.int32), o.view(torch.int32)), (k, f)
+            got = bits(outs[1].index_select(1, torch.as_tensor(idx, device="cuda")))
+            assert np.array_equal(got, obits(exp)), (k, f)
+
+
 # --------------------------------------------------------- the workloads
 @pytest.mark.parametrize("fmt", FMTS)
 def test_mwc_4096x4096_full(fmt):
