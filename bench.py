@@ -71,7 +71,7 @@ def parse():
     p.add_argument("--lanes", type=int, default=2,
                    help="batched: groups of instances whose waves overlap")
     p.add_argument("--no-verify", action="store_true", help="batched: skip the check pass")
-    p.add_argument("--chunk-rows", type=int, default=256,
+    p.add_argument("--chunk-rows", type=int, default=1024,
                    help="batched: rows per piece (0 = whole instances)")
     return p.parse_args()
 

@@ -1,10 +1,12 @@
 """The batched configuration as the benchmark runs it: instances cut into
-256-row pieces, packed into waves on two lanes (scheduler.laned_waves), each
+1024-row pieces (and 256-row ones), packed into waves on two lanes
+(scheduler.laned_waves), each
 wave one persistent launch captured in a CUDA graph, a lane's waves in order
 on its own stream and the two lanes overlapping (laned.LanedGraphs).  The
-recipe is the 10,000-instance one scaled down (300 instances, streams and
-outputs log-uniform up to 4096) with a wave budget small enough for many
-waves, so that most instances carry their state across waves.
+recipe is the 10,000-instance one scaled down (300 instances, streams
+log-uniform up to 4096, outputs up to 16 times the piece length) with a wave
+budget small enough for many waves, so that many instances carry their state
+across waves.
 
 Every piece is checked against the same rows of a plain call of its
 instance, every final state against the plain generator's, and every
@@ -30,15 +32,16 @@ def _built():
     capi.lib()
 
 
-def test_laned_graph_waves_equal_plain_calls_and_oracle():
+@pytest.mark.parametrize("chunk,min_carried", [(1024, 60), (256, 100)])
+def test_laned_graph_waves_equal_plain_calls_and_oracle(chunk, min_carried):
     inst = workloads.batched_instances(300, 4321, streams_range=(32, 4096),
-                                       steps_range=(16, 4096))
+                                       steps_range=(16, 16 * chunk))
     n_streams = [i.n_streams for i in inst]
     rows = [i.n_per_stream for i in inst]
-    pairs = scheduler.laned_waves(n_streams, rows, 16 << 20, 256, 2)
+    pairs = scheduler.laned_waves(n_streams, rows, 16 << 20, chunk, 2)
     assert len(pairs) >= 20 and {lane for lane, _ in pairs} == {0, 1}
     carried = {p.inst for _, w in pairs for p in w if p.row0 > 0}
-    assert len(carried) > 100  # most instances span several waves
+    assert len(carried) > min_carried  # many instances span several waves
 
     # one region per wave, so that every piece can be read back afterwards
     sizes = [laned.wave_elems(w, n_streams) for _, w in pairs]
