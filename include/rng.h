@@ -351,8 +351,9 @@ typedef struct rng_plan *rng_plan_handle;
  * persistent grid puts on each SM (1..32; 0 = as many as fit); both 0 = the
  * default shape, CTAs of 512 threads, one per SM (the fastest measured on
  * GB300).  With ctas_per_sm = 1 the launch reserves more than half an SM's
- * shared memory (unused) so that no SM takes a second CTA.  Items of the same handle must cover disjoint stream
- * ranges (they then run side by side); items with n_per_stream = 0 are
+ * shared memory (unused) so that no SM takes a second CTA.  Items of the
+ * same handle must cover disjoint stream ranges (they then run side by
+ * side); items with n_per_stream = 0 are
  * skipped.  The plan refers to the handles' device
  * memory and the out pointers: it must not outlive them.  Items must be
  * of the kinds RNG_MWC32, RNG_XOR128 or RNG_KISS (the persistent kernel
@@ -511,8 +512,8 @@ int rng_server_set_tick_bytes(rng_server_handle s, uint64_t bytes);
 
 /* Shape of the engine's persistent kernel, as rng_plan_create's `threads`
  * (a power of two in [32, 512]; default 512) and `ctas_per_sm` (0 = as many
- * as fit; default 1).  Synchronises the engine's streams if ticks have run; the next
- * tick of each lane uses the new shape.  Output is the same for any shape.
+ * as fit; default 1).  Synchronises the engine's streams if ticks have run;
+ * the next tick of each lane uses the new shape.  Output is the same for any shape.
  * RNG_ERR_ARG outside those ranges. */
 int rng_server_set_plan_shape(rng_server_handle s, int threads, int ctas_per_sm);
 

@@ -202,10 +202,12 @@ void launch_mixed(int kind, int grid, int threads, bool one_per_sm, cudaStream_t
 }
 
 // Plan shape when the caller passes 0 for both: CTAs of 512 threads, one per
-// SM.  Measured on GB300 with the 10,000-instance workload: 914 GSamples/s
-// with 128 threads (as many CTAs as fit), about 1570 with 512 (two per SM);
-// then, on one box, 1605 with two CTAs of 512 per SM, 1632 with one, 1504
-// with two of 256.  Serving, saturating: 1631 with two, 1641 with one.
+// SM.  Measured on GB300 with the 10,000-instance workload (256-row pieces):
+// 914 GSamples/s with 128 threads (as many CTAs as fit), about 1570 with 512
+// (two per SM); then, on one box, 1605 with two CTAs of 512 per SM, 1641
+// with one (1632 with the grid alone keeping to one, without the
+// shared-memory reservation), 1504 with two of 256.  Serving, saturating:
+// 1631 with two, 1664 with one.
 constexpr int kDefaultThreads = 512;
 constexpr int kDefaultCtas = 1;
 constexpr int kHint = 1;  // streaming stores, as the plain kernels

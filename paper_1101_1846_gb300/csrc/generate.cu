@@ -22,10 +22,12 @@ struct Shape {
     int hint;
     int one;
 };
-// MWC and xor128 uint32 write their rows through TMA bulk copies (hint 2):
-// 6 % and 1.4 % faster per launch on GB300 than 16-byte stores; the FP32
-// forms measured the same, and KISS and XORSHIFT8, whose steps cost more,
-// ran 4-40 % slower that way.  Per-warp bulk copies of 512 B (each warp
+// MWC uint32 writes its rows through TMA bulk copies (hint 2): 6 % faster
+// per launch on GB300 than 16-byte stores from two CTAs per SM, level with
+// them from one.  xor128 uint32 was 1.4 % faster through TMA until 16-byte
+// stores from one CTA per SM overtook it (below); the FP32 forms measured
+// the same, and KISS and XORSHIFT8, whose steps cost more, ran 4-40 %
+// slower that way.  Per-warp bulk copies of 512 B (each warp
 // staging its own rows, no block barrier) were slower than both.
 //
 // Two size classes: calls of fewer than kSmallStreams streams (class 0) and
