@@ -22,7 +22,7 @@ from .generator import BatchItem, Generator, Plan
 
 PLAIN_CANDIDATES = ([(v, b, h, 0) for v in (1, 2) for b in (128, 256, 512) for h in (0, 1)] +
                     [(v, 512, h, 1) for v in (1, 2) for h in (0, 1)])
-PLAN_CANDIDATES = [(64, 0), (128, 0), (256, 0), (512, 0), (128, 4), (256, 2)]
+PLAN_CANDIDATES = [(512, 1), (64, 0), (128, 0), (256, 0), (512, 0), (128, 4), (256, 2)]
 
 
 def _time(fn, reps: int, stream) -> float:
